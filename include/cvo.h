@@ -1,0 +1,189 @@
+/*
+ * cvo.h -- C ABI of the GB300 (sm_103a) implementation of Continuous Visual
+ * Odometry (Ghaffari, Clark, Bloch, Eustice, Grizzle, "Continuous Direct
+ * Sparse Visual Odometry from RGB-D Images", arXiv 1904.02266).
+ *
+ * Two coloured point clouds become functions in an RKHS and the relative pose
+ * is found by gradient ascent on their inner product (Problem 1, Eq. max):
+ *
+ *   F(P) = sum_ij c_ij k(x_i, R z_j + T),   k(x,y) = sigma^2 exp(-|x-y|^2 / 2 ell^2)
+ *
+ * X = {x_i} is the TARGET (fixed) cloud and Z = {z_j} the SOURCE (moving)
+ * cloud. A pose P is a row-major 4x4 double matrix [R T; 0 1] that maps source
+ * coordinates into the target frame; it is the paper's h^{-1} (Sec. 3, where
+ * z~_j = h^{-1} z_j). The solver updates P <- exp(t xi) P (the paper's
+ * h <- h exp(t xi) with xi negated, Eq. newstep), so gradients returned here
+ * are ascent directions for that left update.
+ *
+ * All entry points return an int status: CVO_OK (0) or a negative CVO_ERR_*
+ * code; cvo_strerror() names it and cvo_last_error() gives the context's
+ * detail message. Nothing throws across this boundary. Calls on one context
+ * are serialised by an internal lock; use one context per host thread for
+ * concurrency.
+ *
+ * Memory: every host array is read during the call and stays owned by the
+ * caller. With CVO_DEVICE_PTR the arrays are device pointers on the context's
+ * device; they are read on the given stream (or the context stream when NULL)
+ * before the call returns and are never freed by the library. Clouds are
+ * copied into library-owned device memory, accounted against the context's
+ * HBM budget, and live until cvo_release_cloud or cvo_destroy.
+ */
+#ifndef CVO_H
+#define CVO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CVO_OK 0
+#define CVO_ERR_INVALID_ARG (-1)   /* bad size, pointer, handle or non-finite input */
+#define CVO_ERR_OUT_OF_BUDGET (-2) /* the HBM budget given to cvo_create is exhausted */
+#define CVO_ERR_CUDA (-3)          /* a CUDA runtime call failed (see cvo_last_error) */
+#define CVO_ERR_TIMEOUT (-4)       /* a bounded wait expired */
+#define CVO_ERR_BUSY (-5)          /* no free request slot */
+#define CVO_ERR_NOT_FOUND (-6)     /* unknown cloud handle or ticket */
+#define CVO_ERR_INTERNAL (-7)      /* broken internal invariant */
+
+/* ---- label inner product c_ij (Sec. 2 remark defining c_ij) ------------- */
+#define CVO_COLOR_NONE 0   /* c_ij = 1 */
+#define CVO_COLOR_KERNEL 1 /* c_ij = exp(-|f_i - g_j|^2 / 2 ell_color^2) (appearance kernel) */
+#define CVO_COLOR_DOT 2    /* c_ij = color_scale <f_i, g_j>, the paper's choice (Sec. 5 remark) */
+
+/* ---- lengthscale schedule ---------------------------------------------- */
+#define CVO_SCHEDULE_DECAY 0  /* ell_{k+1} = max(ell_k * ell_decay, ell_min) */
+#define CVO_SCHEDULE_TABLE1 1 /* Table 1: 0.15, then 0.10 after iteration 3, 0.06 after 10, 0.03 after 20 */
+
+/* ---- cvo_set_cloud flags ----------------------------------------------- */
+#define CVO_DEVICE_PTR 1u /* xyz / feat are device pointers */
+
+#define CVO_MAX_FEAT 8    /* largest feature (label) dimension */
+
+typedef struct cvo_ctx cvo_ctx;
+
+/* Solver parameters. cvo_params_default() fills the defaults given here. */
+typedef struct {
+    double ell0;        /* initial spatial lengthscale [m]; 0.15 (Table 1) */
+    double ell_decay;   /* per-iteration factor for CVO_SCHEDULE_DECAY; 0.9 */
+    double ell_min;     /* floor of the decay schedule; 0.02 */
+    int schedule;       /* CVO_SCHEDULE_*; DECAY */
+    double sigma;       /* kernel signal std: k = sigma^2 exp(...); 1.0 */
+    double kcut;        /* sparsification (Sec. 5): pairs with exp(-d^2/2ell^2) < kcut
+                           are dropped, i.e. d > ell sqrt(2 ln(1/kcut)); 1e-3. Must be
+                           in (0, 1): the cell list needs a finite radius. */
+    int color_mode;     /* CVO_COLOR_*; KERNEL */
+    double ell_color;   /* appearance lengthscale for CVO_COLOR_KERNEL; 0.1 */
+    double color_scale; /* scale s for CVO_COLOR_DOT; 1e-5 (Sec. 5 remark) */
+    double a2, b2;      /* metric weights of Eq. metric (n = 3): a^2 |omega|^2 + b^2 |v|^2; 1, 1 */
+    int max_iters;      /* iteration cap; 200 */
+    double eps_pose;    /* stop when |t xi| < eps_pose at the lengthscale floor; 1e-5 (Table 1) */
+    double eps_grad;    /* ... or when |xi| < eps_grad there; 5e-5 (Table 1) */
+    int step_order;     /* 4: first maximiser of the quartic Taylor model (Eq. fourth); 2: quadratic */
+    int feat_dim;       /* feature dimension D in [0, CVO_MAX_FEAT]; 5. 0 forces COLOR_NONE */
+    double cell_factor; /* cell edge of the target grid as a multiple of the cutoff radius; 1.0 */
+} cvo_params;
+
+/* One evaluation at a fixed pose (cvo_eval). */
+typedef struct {
+    double F;          /* F = sum_ij c_ij k_ij over kept pairs (Eq. scalar) */
+    double grad6[6];   /* metric gradient xi = (omega, v): dF/domega / a^2, dF/dv / b^2
+                          (Eq. 3_gradient under the left update) */
+    double S[5];       /* S0..S4: G(t) = F(exp(t xi) P) ~ S0 + S1 t + ... + S4 t^4 along
+                          xi = grad6 (Eq. fourth) */
+    int64_t nnz;       /* pairs kept (d <= r_c) in the gradient pass */
+    int64_t candidates;/* candidate pairs visited by the cell-list traversal */
+} cvo_eval_result;
+
+/* Statistics of one solve (cvo_align, cvo_poll). */
+typedef struct {
+    int iters;            /* iterations run */
+    int converged;        /* 1 if the Table 1 test fired before max_iters */
+    int fallback_steps;   /* iterations whose quartic had no maximiser on t > 0 */
+    int no_ascent_steps;  /* iterations with S1 <= 0 (no step taken) */
+    double final_ell;     /* lengthscale of the last iteration */
+    double F_last;        /* F at the last evaluated pose */
+    double t_last;        /* last step length */
+    int64_t pair_evals;   /* kept pairs summed over every gradient and step pass */
+    int64_t candidates;   /* candidate pairs visited over every pass */
+    int status;           /* CVO_OK or the error that ended the solve */
+} cvo_stats;
+
+/* Fill *p with the defaults listed in cvo_params. */
+void cvo_params_default(cvo_params* p);
+
+/* Create a context on CUDA device `device` with its own stream. Device memory
+ * the context allocates for clouds, grids and solves is limited to
+ * hbm_budget_bytes (0 = no limit). Returns CVO_ERR_INVALID_ARG for bad
+ * parameters, CVO_ERR_CUDA if the device cannot be used. */
+int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cvo_ctx** out);
+
+/* Free every resource of the context (clouds, grids, graphs, stream). */
+int cvo_destroy(cvo_ctx* ctx);
+
+/* Upload a cloud: xyz is n x 3 float32 (row-major), feat is n x feat_dim
+ * float32 (ignored, may be NULL, when feat_dim == 0 or color_mode is NONE).
+ * The library centres the cloud on its FP64 centroid, packs it
+ * structure-of-arrays, orders it along a Morton curve for use as a source, and
+ * builds the target cell lists lazily. Errors: CVO_ERR_INVALID_ARG for n <= 0,
+ * n > 2^22, NULL pointers or any non-finite value (checked on the device);
+ * CVO_ERR_OUT_OF_BUDGET if the copy would exceed the budget. */
+int cvo_set_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, uint32_t flags,
+                  void* stream, int32_t* handle_out);
+
+/* Release a cloud and every cached grid and plan that uses it. */
+int cvo_release_cloud(cvo_ctx* ctx, int32_t handle);
+
+/* One gradient pass and one step pass at pose P and lengthscale ell
+ * (Eqs. scalar, 3_gradient, metric, fourth). Synchronous: results are in
+ * *out when it returns. */
+int cvo_eval(cvo_ctx* ctx, int32_t target, int32_t source, const double P[16], double ell,
+             cvo_eval_result* out);
+
+/* Full solve from P0 (Problem 1; Eqs. flow, fourth, newstep, step): gradient,
+ * step sums, quartic step and exponential-map update per iteration, with the
+ * lengthscale schedule of the context. The whole loop runs on the device as
+ * one CUDA graph with a device-side while loop. Synchronous. P_out receives
+ * the final pose; stats (may be NULL) the solve statistics. */
+int cvo_align(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
+              double P_out[16], cvo_stats* stats);
+
+/* Per-iteration record of cvo_align_profile. */
+typedef struct {
+    double ell;               /* lengthscale of the iteration */
+    float plan_ms;            /* CUDA-event duration of the traversal plan (cell rows per cluster) */
+    float grad_ms, step_ms;   /* CUDA-event durations of the gradient and step pair passes */
+    int64_t grad_pairs;       /* pairs kept in the gradient pass */
+    int64_t step_pairs;       /* pairs kept in the step pass */
+    int64_t grad_candidates;  /* candidates visited in the gradient pass */
+    int64_t step_candidates;  /* candidates visited in the step pass */
+} cvo_iter_profile;
+
+/* The same solve as cvo_align (same plan, kernels and results) with the
+ * iteration loop driven from the host instead of the device-side graph loop,
+ * so that each pair pass can be bracketed by CUDA events on the context
+ * stream. Slower than cvo_align (one host round trip per iteration); meant
+ * for measurement. Writes min(iters, max_records) records and the count to
+ * *n_records (may be NULL). */
+int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
+                      double P_out[16], cvo_stats* stats, cvo_iter_profile* records,
+                      int max_records, int* n_records);
+
+/* The context's CUDA stream (cudaStream_t), on which every kernel of the
+ * context runs; NULL for a NULL context. */
+void* cvo_stream(cvo_ctx* ctx);
+
+/* Name of a status code (static string). */
+const char* cvo_strerror(int status);
+
+/* Detail message of the last failed call on this context (static until the
+ * next call on the context; "" if none). */
+const char* cvo_last_error(cvo_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CVO_H */

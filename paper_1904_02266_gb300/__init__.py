@@ -1,0 +1,307 @@
+"""GB300-native Continuous Visual Odometry (CVO, arXiv 1904.02266).
+
+Thin ctypes binding over ``libcvo.so``, whose C ABI is declared in
+``include/cvo.h``. Every step of the solve runs in the library's CUDA kernels;
+this module only marshals arguments. Functions named like the C entry points
+(``cvo_create``, ``cvo_set_cloud``, ``cvo_eval``, ``cvo_align``, ...) map one
+to one onto them; ``Context`` wraps them for convenience.
+
+Host arrays (numpy) are copied by the library; CUDA tensors (torch) are passed
+as device pointers with the current torch stream. There is no fallback: if the
+library has not been built, importing the binding works but the first call
+raises ``CvoUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB as LIB_PATH
+
+CVO_OK = 0
+CVO_ERR_INVALID_ARG = -1
+CVO_ERR_OUT_OF_BUDGET = -2
+CVO_ERR_CUDA = -3
+CVO_ERR_TIMEOUT = -4
+CVO_ERR_BUSY = -5
+CVO_ERR_NOT_FOUND = -6
+CVO_ERR_INTERNAL = -7
+
+CVO_COLOR_NONE, CVO_COLOR_KERNEL, CVO_COLOR_DOT = 0, 1, 2
+CVO_SCHEDULE_DECAY, CVO_SCHEDULE_TABLE1 = 0, 1
+CVO_DEVICE_PTR = 1
+CVO_MAX_FEAT = 8
+
+# every entry point declared in include/cvo.h
+EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
+           "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile", "cvo_stream",
+           "cvo_strerror", "cvo_last_error")
+
+
+class CvoUnavailable(RuntimeError):
+    """libcvo.so is missing or cannot be loaded."""
+
+
+class CvoError(RuntimeError):
+    def __init__(self, code, detail=""):
+        self.code = code
+        super().__init__(f"{strerror(code)} ({code}): {detail}" if detail else strerror(code))
+
+
+class cvo_params(ctypes.Structure):
+    _fields_ = [("ell0", ctypes.c_double), ("ell_decay", ctypes.c_double),
+                ("ell_min", ctypes.c_double), ("schedule", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("kcut", ctypes.c_double),
+                ("color_mode", ctypes.c_int), ("ell_color", ctypes.c_double),
+                ("color_scale", ctypes.c_double), ("a2", ctypes.c_double),
+                ("b2", ctypes.c_double), ("max_iters", ctypes.c_int),
+                ("eps_pose", ctypes.c_double), ("eps_grad", ctypes.c_double),
+                ("step_order", ctypes.c_int), ("feat_dim", ctypes.c_int),
+                ("cell_factor", ctypes.c_double)]
+
+
+class cvo_eval_result(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_double), ("grad6", ctypes.c_double * 6),
+                ("S", ctypes.c_double * 5), ("nnz", ctypes.c_int64),
+                ("candidates", ctypes.c_int64)]
+
+
+class cvo_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("fallback_steps", ctypes.c_int), ("no_ascent_steps", ctypes.c_int),
+                ("final_ell", ctypes.c_double), ("F_last", ctypes.c_double),
+                ("t_last", ctypes.c_double), ("pair_evals", ctypes.c_int64),
+                ("candidates", ctypes.c_int64), ("status", ctypes.c_int)]
+
+
+class cvo_iter_profile(ctypes.Structure):
+    _fields_ = [("ell", ctypes.c_double), ("plan_ms", ctypes.c_float), ("grad_ms", ctypes.c_float),
+                ("step_ms", ctypes.c_float), ("grad_pairs", ctypes.c_int64),
+                ("step_pairs", ctypes.c_int64), ("grad_candidates", ctypes.c_int64),
+                ("step_candidates", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libcvo.so and declare its signatures. Raises CvoUnavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise CvoUnavailable(f"{path} is not built; run __graft_entry__.build() "
+                                 f"(or python -m paper_1904_02266_gb300.build)")
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError as e:
+            raise CvoUnavailable(f"cannot load {path}: {e}") from e
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        lib.cvo_params_default.argtypes = [ctypes.POINTER(cvo_params)]
+        lib.cvo_params_default.restype = None
+        lib.cvo_create.argtypes = [ctypes.POINTER(cvo_params), ctypes.c_int, ctypes.c_size_t,
+                                   ctypes.POINTER(vp)]
+        lib.cvo_destroy.argtypes = [vp]
+        lib.cvo_set_cloud.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_uint32, vp,
+                                      ctypes.POINTER(ctypes.c_int32)]
+        lib.cvo_release_cloud.argtypes = [vp, ctypes.c_int32]
+        lib.cvo_eval.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, dp, ctypes.c_double,
+                                 ctypes.POINTER(cvo_eval_result)]
+        lib.cvo_align.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, dp, dp,
+                                  ctypes.POINTER(cvo_stats)]
+        lib.cvo_align_profile.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, dp, dp,
+                                          ctypes.POINTER(cvo_stats),
+                                          ctypes.POINTER(cvo_iter_profile), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]
+        lib.cvo_align_profile.restype = ctypes.c_int
+        lib.cvo_stream.argtypes = [vp]
+        lib.cvo_stream.restype = ctypes.c_void_p
+        lib.cvo_strerror.argtypes = [ctypes.c_int]
+        lib.cvo_strerror.restype = ctypes.c_char_p
+        lib.cvo_last_error.argtypes = [vp]
+        lib.cvo_last_error.restype = ctypes.c_char_p
+        for name in ("cvo_create", "cvo_destroy", "cvo_set_cloud", "cvo_release_cloud",
+                     "cvo_eval", "cvo_align"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load_library().cvo_strerror(int(code)).decode()
+    except CvoUnavailable:
+        return f"status {code}"
+
+
+def _check(ctx, code):
+    if code != CVO_OK:
+        detail = load_library().cvo_last_error(ctx).decode() if ctx else ""
+        raise CvoError(code, detail)
+
+
+def _pose(P):
+    a = np.ascontiguousarray(np.asarray(P, dtype=np.float64).reshape(4, 4))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---------------------------------------------------------------------------
+# one function per C entry point
+# ---------------------------------------------------------------------------
+
+def cvo_params_default() -> cvo_params:
+    p = cvo_params()
+    load_library().cvo_params_default(ctypes.byref(p))
+    return p
+
+
+def cvo_create(params: cvo_params | None = None, device: int = 0, hbm_budget_bytes: int = 0):
+    lib = load_library()
+    out = ctypes.c_void_p()
+    code = lib.cvo_create(ctypes.byref(params) if params is not None else None, int(device),
+                          int(hbm_budget_bytes), ctypes.byref(out))
+    _check(None, code)
+    return out
+
+
+def cvo_destroy(ctx) -> None:
+    _check(None, load_library().cvo_destroy(ctx))
+
+
+def cvo_set_cloud(ctx, xyz, feat=None, n=None, flags=0, stream=None) -> int:
+    """xyz: (n, 3) float32; feat: (n, D) float32 or None. numpy arrays are host
+    buffers; objects with ``data_ptr()`` and ``is_cuda`` (torch tensors) are
+    passed as device pointers."""
+    keep = []
+
+    def ptr(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+            if not a.is_contiguous() or str(a.dtype) != "torch.float32":
+                raise ValueError("device arrays must be contiguous float32")
+            return a.data_ptr()
+        arr = np.ascontiguousarray(a, dtype=np.float32)
+        keep.append(arr)
+        return arr.ctypes.data
+
+    dev = hasattr(xyz, "data_ptr") and getattr(xyz, "is_cuda", False)
+    if dev:
+        flags |= CVO_DEVICE_PTR
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(xyz.device).cuda_stream
+    n = int(xyz.shape[0]) if n is None else int(n)
+    h = ctypes.c_int32(-1)
+    code = load_library().cvo_set_cloud(ctx, ptr(xyz), ptr(feat), n, int(flags),
+                                        stream if stream else None, ctypes.byref(h))
+    _check(ctx, code)
+    return int(h.value)
+
+
+def cvo_release_cloud(ctx, handle: int) -> None:
+    _check(ctx, load_library().cvo_release_cloud(ctx, int(handle)))
+
+
+def cvo_eval(ctx, target: int, source: int, P, ell: float) -> dict:
+    _, pp = _pose(P)
+    r = cvo_eval_result()
+    _check(ctx, load_library().cvo_eval(ctx, int(target), int(source), pp, float(ell),
+                                        ctypes.byref(r)))
+    return {"F": r.F, "grad6": np.array(r.grad6[:]), "S": np.array(r.S[:]), "nnz": int(r.nnz),
+            "candidates": int(r.candidates)}
+
+
+def cvo_align(ctx, target: int, source: int, P0=None):
+    _, p0 = _pose(np.eye(4) if P0 is None else P0)
+    out = np.zeros((4, 4))
+    st = cvo_stats()
+    _check(ctx, load_library().cvo_align(ctx, int(target), int(source), p0,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.byref(st)))
+    stats = {k: getattr(st, k) for k, _ in cvo_stats._fields_}
+    return out, stats
+
+
+def cvo_align_profile(ctx, target: int, source: int, P0=None, max_records: int = 1000):
+    """cvo_align with per-iteration CUDA-event timings of both pair passes."""
+    _, p0 = _pose(np.eye(4) if P0 is None else P0)
+    out = np.zeros((4, 4))
+    st = cvo_stats()
+    recs = (cvo_iter_profile * max(1, max_records))()
+    nrec = ctypes.c_int(0)
+    _check(ctx, load_library().cvo_align_profile(
+        ctx, int(target), int(source), p0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        ctypes.byref(st), recs, int(max_records), ctypes.byref(nrec)))
+    stats = {k: getattr(st, k) for k, _ in cvo_stats._fields_}
+    records = [{k: getattr(recs[i], k) for k, _ in cvo_iter_profile._fields_}
+               for i in range(nrec.value)]
+    return out, stats, records
+
+
+def cvo_stream(ctx) -> int:
+    """The context's cudaStream_t as an integer (for CUDA events on it)."""
+    return int(load_library().cvo_stream(ctx) or 0)
+
+
+def cvo_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def cvo_last_error(ctx) -> str:
+    return load_library().cvo_last_error(ctx).decode()
+
+
+class Context:
+    """One library context: clouds, cached cell lists and solve plans on one GPU."""
+
+    def __init__(self, params: cvo_params | None = None, device: int = 0, hbm_budget: int = 0,
+                 **overrides):
+        p = cvo_params_default() if params is None else params
+        for k, v in overrides.items():
+            if not hasattr(p, k):
+                raise AttributeError(f"cvo_params has no field {k!r}")
+            setattr(p, k, v)
+        self.params = p
+        self.ctx = cvo_create(p, device, hbm_budget)
+
+    def set_cloud(self, xyz, feat=None, stream=None) -> int:
+        return cvo_set_cloud(self.ctx, xyz, feat, stream=stream)
+
+    def release(self, handle: int) -> None:
+        cvo_release_cloud(self.ctx, handle)
+
+    def eval(self, target: int, source: int, P, ell: float) -> dict:
+        return cvo_eval(self.ctx, target, source, P, ell)
+
+    def align(self, target: int, source: int, P0=None):
+        return cvo_align(self.ctx, target, source, P0)
+
+    def align_profile(self, target: int, source: int, P0=None, max_records: int = 1000):
+        return cvo_align_profile(self.ctx, target, source, P0, max_records)
+
+    @property
+    def stream(self) -> int:
+        return cvo_stream(self.ctx)
+
+    def close(self) -> None:
+        if self.ctx:
+            cvo_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,897 @@
+// Host runtime behind the C ABI in include/cvo.h: contexts, clouds, cached
+// target cell lists, solve plans and the CUDA graph that runs a whole solve on
+// the device (Problem 1 iterated by a while-conditional graph node, no host
+// round trip per iteration).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/cvo.h"
+#include "cvo_internal.cuh"
+
+using namespace cvo;
+
+namespace {
+
+struct Grid {
+  double h_req = 0.0;   // requested cell edge (cache key)
+  GridView view{};
+  float4* xyz = nullptr;
+  float* feat = nullptr;
+  int* cell_start = nullptr;
+  size_t bytes = 0;
+};
+
+struct Clusters {
+  float max_edge = 0.f;  // cache key
+  int* cstart = nullptr;
+  int ncl = 0;
+  size_t bytes = 0;
+};
+
+struct Cloud {
+  int64_t n = 0;
+  int n_pad = 0;
+  int D = 0, dp = 0;
+  double c[3] = {0, 0, 0};
+  float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // bounding box, centred frame
+  MortonFrame mf{};
+  float4* xyz = nullptr;  // packed, original order
+  float* feat = nullptr;
+  float4* zs = nullptr;   // Morton order (source role)
+  float* zf = nullptr;
+  std::vector<Grid> grids;
+  std::vector<Clusters> clusters;
+  size_t bytes = 0;
+};
+
+struct Plan {
+  int tgt = -1, src = -1;
+  SolveCfg h_cfg{};
+  SolveCfg* d_cfg = nullptr;
+  IterConst* d_iters = nullptr;
+  SolveState* d_state = nullptr;
+  double* d_partials = nullptr;
+  float4* zt = nullptr;
+  int* seg_xs = nullptr;
+  int* seg_pref = nullptr;
+  int* cl_nseg = nullptr;
+  int* cl_cand = nullptr;
+  int* chunk_pref = nullptr;
+  int* warp_start = nullptr;
+  int cap_iters = 0, cap_ncl = 0, cap_m_pad = 0;
+  int nblocks = 0;
+  int ncl_launch = 0;
+  int n_iters = 0;
+  int dp = 0, color_mode = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct cvo_ctx {
+  int device = 0;
+  int sms = 0;
+  cvo_params prm{};
+  size_t budget = 0, used = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<Cloud*> clouds;
+  std::map<std::pair<int, int>, Plan*> plans;
+  Plan* eval_plan = nullptr;      // reused by cvo_eval
+  SolveState* h_state = nullptr;  // pinned
+  CloudStats* d_stats = nullptr;
+  CloudStats* h_stats = nullptr;  // pinned
+  int* h_int = nullptr;           // pinned scratch for small read-backs
+  std::string err;
+  std::mutex mu;
+};
+
+namespace {
+
+int fail(cvo_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(ctx, CVO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int dev_alloc(cvo_ctx* ctx, void** p, size_t bytes, size_t* acct) {
+  *p = nullptr;
+  if (ctx->budget > 0 && ctx->used + bytes > ctx->budget)
+    return fail(ctx, CVO_ERR_OUT_OF_BUDGET, "HBM budget exhausted");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, CVO_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  if (acct) *acct += bytes;
+  return CVO_OK;
+}
+
+void release_bytes(cvo_ctx* ctx, size_t bytes) { ctx->used -= bytes <= ctx->used ? bytes : ctx->used; }
+
+int padded_dim(const cvo_params& p) {
+  if (p.color_mode == CVO_COLOR_NONE || p.feat_dim == 0) return 0;
+  if (p.feat_dim <= 3) return 3;
+  if (p.feat_dim <= 5) return 5;
+  return 8;
+}
+
+// Feature pre-scale: for the appearance kernel, sqrt(log2(e) / (2 ell_c^2)) so
+// that |f'_i - g'_j|^2 is the base-2 exponent; for the dot product, sqrt(s).
+float feature_scale(const cvo_params& p) {
+  if (p.color_mode == CVO_COLOR_KERNEL)
+    return (float)std::sqrt(1.4426950408889634 / (2.0 * p.ell_color * p.ell_color));
+  if (p.color_mode == CVO_COLOR_DOT) return (float)std::sqrt(p.color_scale);
+  return 1.0f;
+}
+
+double cutoff_radius(const cvo_params& p, double ell) {
+  return ell * std::sqrt(2.0 * std::log(1.0 / p.kcut));
+}
+
+Cloud* get_cloud(cvo_ctx* ctx, int32_t h) {
+  if (h < 0 || h >= (int32_t)ctx->clouds.size()) return nullptr;
+  return ctx->clouds[h];
+}
+
+void free_grid(cvo_ctx* ctx, Grid& g) {
+  cudaFree(g.xyz);
+  cudaFree(g.feat);
+  cudaFree(g.cell_start);
+  release_bytes(ctx, g.bytes);
+  g = Grid();
+}
+
+void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
+  cudaFree(p->d_cfg);
+  cudaFree(p->d_iters);
+  cudaFree(p->d_state);
+  cudaFree(p->d_partials);
+  cudaFree(p->zt);
+  cudaFree(p->seg_xs);
+  cudaFree(p->seg_pref);
+  cudaFree(p->cl_nseg);
+  cudaFree(p->cl_cand);
+  cudaFree(p->chunk_pref);
+  cudaFree(p->warp_start);
+  release_bytes(ctx, p->bytes);
+  p->d_cfg = nullptr;
+  p->d_iters = nullptr;
+  p->d_state = nullptr;
+  p->d_partials = nullptr;
+  p->zt = nullptr;
+  p->seg_xs = p->seg_pref = p->cl_nseg = p->cl_cand = p->chunk_pref = p->warp_start = nullptr;
+  p->bytes = 0;
+  p->cap_iters = p->cap_ncl = p->cap_m_pad = 0;
+}
+
+void free_plan(cvo_ctx* ctx, Plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  free_plan_buffers(ctx, p);
+  delete p;
+}
+
+void free_cloud(cvo_ctx* ctx, Cloud* c) {
+  if (!c) return;
+  for (Grid& g : c->grids) free_grid(ctx, g);
+  for (Clusters& k : c->clusters) {
+    cudaFree(k.cstart);
+    release_bytes(ctx, k.bytes);
+  }
+  cudaFree(c->xyz);
+  cudaFree(c->feat);
+  cudaFree(c->zs);
+  cudaFree(c->zf);
+  release_bytes(ctx, c->bytes);
+  delete c;
+}
+
+// Cell list of edge >= h_req over target cloud c (cached per requested edge).
+int ensure_grid(cvo_ctx* ctx, Cloud* c, double h_req, int* index_out) {
+  for (size_t i = 0; i < c->grids.size(); ++i)
+    if (c->grids[i].h_req == h_req) {
+      *index_out = (int)i;
+      return CVO_OK;
+    }
+  Grid g;
+  g.h_req = h_req;
+  double h = h_req;
+  int nx, ny, nz;
+  for (;;) {
+    nx = (int)std::floor((c->hi[0] - c->lo[0]) / h) + 1;
+    ny = (int)std::floor((c->hi[1] - c->lo[1]) / h) + 1;
+    nz = (int)std::floor((c->hi[2] - c->lo[2]) / h) + 1;
+    if ((double)nx * ny * nz <= (double)kMaxCells) break;
+    h *= 1.25;  // a coarser grid visits more candidates but stays exact
+  }
+  const int ncells = nx * ny * nz;
+  const int n = (int)c->n;
+  int rc = dev_alloc(ctx, (void**)&g.xyz, sizeof(float4) * c->n_pad, &g.bytes);
+  if (rc == CVO_OK && c->dp > 0)
+    rc = dev_alloc(ctx, (void**)&g.feat, sizeof(float) * c->dp * (size_t)c->n_pad, &g.bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&g.cell_start, sizeof(int) * (ncells + 1), &g.bytes);
+  if (rc != CVO_OK) {
+    free_grid(ctx, g);
+    return rc;
+  }
+  const float hf = (float)h;
+  cudaError_t e = build_grid(c->xyz, c->feat, n, c->dp, c->n_pad, nx, ny, nz, c->lo[0], c->lo[1],
+                             c->lo[2], hf, g.xyz, g.feat, g.cell_start, ctx->stream);
+  if (e != cudaSuccess) {
+    free_grid(ctx, g);
+    return fail(ctx, CVO_ERR_CUDA, std::string("build_grid: ") + cudaGetErrorString(e));
+  }
+  GridView& v = g.view;
+  v.xyz = g.xyz;
+  v.feat = g.feat;
+  v.cell_start = g.cell_start;
+  v.n = n;
+  v.n_pad = c->n_pad;
+  v.nx = nx;
+  v.ny = ny;
+  v.nz = nz;
+  v.ox = c->lo[0];
+  v.oy = c->lo[1];
+  v.oz = c->lo[2];
+  v.h = hf;
+  v.inv_h = 1.0f / hf;
+  c->grids.push_back(g);
+  *index_out = (int)c->grids.size() - 1;
+  return CVO_OK;
+}
+
+// Source clusters whose octree nodes have edge <= max_edge (cached).
+int ensure_clusters(cvo_ctx* ctx, Cloud* c, float max_edge, int* index_out) {
+  for (size_t i = 0; i < c->clusters.size(); ++i)
+    if (c->clusters[i].max_edge == max_edge) {
+      *index_out = (int)i;
+      return CVO_OK;
+    }
+  Clusters k;
+  k.max_edge = max_edge;
+  int rc = dev_alloc(ctx, (void**)&k.cstart, sizeof(int) * (c->n + 2), &k.bytes);
+  if (rc != CVO_OK) return rc;
+  int* d_ncl = k.cstart + c->n + 1;
+  cudaError_t e = build_clusters(c->zs, (int)c->n, c->mf, max_edge, k.cstart, d_ncl, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_int, d_ncl, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(k.cstart);
+    release_bytes(ctx, k.bytes);
+    return fail(ctx, CVO_ERR_CUDA, std::string("build_clusters: ") + cudaGetErrorString(e));
+  }
+  k.ncl = *ctx->h_int;
+  c->clusters.push_back(k);
+  *index_out = (int)c->clusters.size() - 1;
+  return CVO_OK;
+}
+
+std::vector<double> ell_schedule(const cvo_params& p, int n) {
+  std::vector<double> out;
+  out.reserve(n);
+  if (p.schedule == CVO_SCHEDULE_TABLE1) {
+    for (int k = 0; k < n; ++k) {
+      const int it = k + 1;
+      out.push_back(it <= 3 ? 0.15 : it <= 10 ? 0.10 : it <= 20 ? 0.06 : 0.03);
+    }
+    return out;
+  }
+  double ell = p.ell0;
+  for (int k = 0; k < n; ++k) {
+    out.push_back(ell);
+    ell = std::max(ell * p.ell_decay, p.ell_min);
+  }
+  return out;
+}
+
+double ell_floor(const cvo_params& p) {
+  return p.schedule == CVO_SCHEDULE_TABLE1 ? 0.03 : p.ell_min;
+}
+
+// Grow the plan's device buffers to the given capacities.
+int reserve_plan(cvo_ctx* ctx, Plan* p, int iters, int ncl, int m_pad, int nblocks) {
+  if (p->d_cfg && iters <= p->cap_iters && ncl <= p->cap_ncl && m_pad <= p->cap_m_pad &&
+      nblocks == p->nblocks)
+    return CVO_OK;
+  free_plan_buffers(ctx, p);
+  iters = std::max(iters, 1);
+  ncl = std::max(ncl, 1);
+  int rc = dev_alloc(ctx, (void**)&p->d_cfg, sizeof(SolveCfg), &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->d_iters, sizeof(IterConst) * iters, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->d_state, sizeof(SolveState), &p->bytes);
+  if (rc == CVO_OK)
+    rc = dev_alloc(ctx, (void**)&p->d_partials, sizeof(double) * kPartialStride * nblocks, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->zt, sizeof(float4) * m_pad, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->seg_xs, sizeof(int) * (size_t)ncl * kMaxSeg, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->seg_pref, sizeof(int) * (size_t)ncl * kMaxSeg, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_nseg, sizeof(int) * ncl, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_cand, sizeof(int) * ncl, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->chunk_pref, sizeof(int) * (ncl + 1), &p->bytes);
+  if (rc == CVO_OK)
+    rc = dev_alloc(ctx, (void**)&p->warp_start, sizeof(int) * nblocks * kWarps, &p->bytes);
+  if (rc != CVO_OK) {
+    free_plan_buffers(ctx, p);
+    return rc;
+  }
+  cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(SolveState), ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e));
+  p->cap_iters = iters;
+  p->cap_ncl = ncl;
+  p->cap_m_pad = m_pad;
+  p->nblocks = nblocks;
+  return CVO_OK;
+}
+
+// Configure a plan for target t, source s and the lengthscales of its
+// iterations: cell lists and clusters per level (a finer level whenever the
+// cutoff radius has shrunk to half the current cell edge), work buffers, the
+// per-iteration constants and the solve configuration on the device.
+int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<double>& ells,
+                   int mode) {
+  const cvo_params& prm = ctx->prm;
+  const double f = prm.cell_factor;
+  std::vector<double> hs;
+  std::vector<int> level_of(ells.size(), 0);
+  double h_cur = -1.0;
+  for (size_t k = 0; k < ells.size(); ++k) {
+    const double rc = cutoff_radius(prm, ells[k]);
+    if (h_cur < 0.0 || (f * rc <= 0.5 * h_cur && (int)hs.size() < kMaxLevels)) {
+      h_cur = f * rc;
+      hs.push_back(h_cur);
+    }
+    level_of[k] = (int)hs.size() - 1;
+  }
+  SolveCfg cfg{};
+  int ncl_max = 0;
+  for (size_t l = 0; l < hs.size(); ++l) {
+    int gi = 0, ki = 0;
+    int rc = ensure_grid(ctx, t, hs[l], &gi);
+    if (rc != CVO_OK) return rc;
+    cfg.grids[l] = t->grids[gi].view;
+    rc = ensure_clusters(ctx, s, 0.5f * t->grids[gi].view.h, &ki);
+    if (rc != CVO_OK) return rc;
+    cfg.clusters[l].cstart = s->clusters[ki].cstart;
+    cfg.clusters[l].ncl = s->clusters[ki].ncl;
+    ncl_max = std::max(ncl_max, s->clusters[ki].ncl);
+  }
+  const int nblocks = 2 * ctx->sms;
+  int rc = reserve_plan(ctx, p, (int)ells.size(), ncl_max, s->n_pad, nblocks);
+  if (rc != CVO_OK) return rc;
+  std::vector<IterConst> ic(ells.size());
+  const double log2e = 1.4426950408889634073599246810019;
+  for (size_t k = 0; k < ells.size(); ++k) {
+    const double ell = ells[k], ell2 = ell * ell;
+    const double rc2 = 2.0 * ell2 * std::log(1.0 / prm.kcut);
+    ic[k].ell = ell;
+    ic[k].inv_l2 = 1.0 / ell2;
+    ic[k].A = (float)(log2e / (2.0 * ell2));
+    ic[k].rc2 = (float)rc2;
+    ic[k].rprune = (float)(std::sqrt(rc2) * 1.001);
+    ic[k].level = level_of[k];
+  }
+  cfg.src.xyz = s->zs;
+  cfg.src.feat = s->zf;
+  cfg.src.m = (int)s->n;
+  cfg.src.m_pad = s->n_pad;
+  cfg.iters = p->d_iters;
+  cfg.zt = p->zt;
+  cfg.seg_xs = p->seg_xs;
+  cfg.seg_pref = p->seg_pref;
+  cfg.cl_nseg = p->cl_nseg;
+  cfg.cl_cand = p->cl_cand;
+  cfg.chunk_pref = p->chunk_pref;
+  cfg.warp_start = p->warp_start;
+  cfg.nblocks = nblocks;
+  cfg.nwarps = nblocks * kWarps;
+  for (int a = 0; a < 3; ++a) {
+    cfg.cX[a] = t->c[a];
+    cfg.cZ[a] = s->c[a];
+  }
+  cfg.sigma2 = prm.sigma * prm.sigma;
+  cfg.a2 = prm.a2;
+  cfg.b2 = prm.b2;
+  cfg.ell_floor = ell_floor(prm);
+  cfg.eps_pose = prm.eps_pose;
+  cfg.eps_grad = prm.eps_grad;
+  cfg.max_iters = mode == kModeEval ? 1 : prm.max_iters;
+  cfg.step_order = prm.step_order;
+  cfg.mode = mode;
+  // pageable sources: the copies complete before the calls return
+  CK(cudaMemcpyAsync(p->d_iters, ic.data(), sizeof(IterConst) * ic.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(p->d_cfg, &cfg, sizeof(SolveCfg), cudaMemcpyHostToDevice, ctx->stream));
+  p->h_cfg = cfg;
+  p->ncl_launch = ncl_max;
+  p->n_iters = (int)ells.size();
+  p->dp = s->dp;
+  p->color_mode = prm.color_mode;
+  return CVO_OK;
+}
+
+// Kernels of one iteration body on stream s.
+cudaError_t launch_iteration(Plan* p, cudaGraphConditionalHandle cond, int use_cond,
+                             cudaStream_t s) {
+  cudaError_t e = launch_plan(p->d_cfg, p->d_state, p->ncl_launch, s);
+  if (e == cudaSuccess)
+    e = launch_pair_pass(false, p->dp, p->color_mode, p->nblocks, p->d_cfg, p->d_state,
+                         p->d_partials, cond, use_cond, s);
+  if (e == cudaSuccess)
+    e = launch_pair_pass(true, p->dp, p->color_mode, p->nblocks, p->d_cfg, p->d_state,
+                         p->d_partials, cond, use_cond, s);
+  return e;
+}
+
+int build_plan(cvo_ctx* ctx, int tgt, int src, Plan** out) {
+  Cloud* t = get_cloud(ctx, tgt);
+  Cloud* s = get_cloud(ctx, src);
+  Plan* p = new Plan();
+  p->tgt = tgt;
+  p->src = src;
+  const int max_iters = std::max(0, ctx->prm.max_iters);
+  std::vector<double> ells = ell_schedule(ctx->prm, std::max(1, max_iters));
+  int rc = configure_plan(ctx, p, t, s, ells, kModeAlign);
+  cudaError_t e = cudaSuccess;
+  if (rc == CVO_OK) e = cudaStreamSynchronize(ctx->stream);
+  // graph: init -> while(cond) { plan -> gradient pass -> step pass }
+  if (rc == CVO_OK && e == cudaSuccess) e = cudaGraphCreate(&p->graph, 0);
+  if (rc == CVO_OK && e == cudaSuccess)
+    e = cudaGraphConditionalHandleCreate(&p->cond, p->graph, 1, cudaGraphCondAssignDefault);
+  cudaGraph_t captured = nullptr;
+  if (rc == CVO_OK && e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, p->graph, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (rc == CVO_OK && e == cudaSuccess) {
+    cudaError_t el = launch_init(p->d_cfg, p->d_state, p->cond, 1, ctx->cap_stream);
+    e = cudaStreamEndCapture(ctx->cap_stream, &captured);
+    if (e == cudaSuccess) e = el;
+  }
+  cudaGraphNode_t cnode;
+  cudaGraphNodeParams cp{};
+  if (rc == CVO_OK && e == cudaSuccess) {
+    size_t nnodes = 0;
+    e = cudaGraphGetNodes(p->graph, nullptr, &nnodes);
+    std::vector<cudaGraphNode_t> nodes(nnodes);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(p->graph, nodes.data(), &nnodes);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = p->cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, p->graph, nodes.data(), nullptr, nnodes, &cp);
+  }
+  if (rc == CVO_OK && e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = launch_iteration(p, p->cond, 1, ctx->cap_stream);
+      e = cudaStreamEndCapture(ctx->cap_stream, &captured);
+      if (e == cudaSuccess) e = el;
+    }
+  }
+  if (rc == CVO_OK && e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (rc == CVO_OK && e != cudaSuccess)
+    rc = fail(ctx, CVO_ERR_CUDA, std::string("solve graph: ") + cudaGetErrorString(e));
+  if (rc != CVO_OK) {
+    free_plan(ctx, p);
+    return rc;
+  }
+  *out = p;
+  return CVO_OK;
+}
+
+int check_pose(cvo_ctx* ctx, const double* P) {
+  if (!P) return fail(ctx, CVO_ERR_INVALID_ARG, "pose pointer is NULL");
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(P[i])) return fail(ctx, CVO_ERR_INVALID_ARG, "pose has a non-finite entry");
+  return CVO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cvo_params_default(cvo_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->ell0 = 0.15;
+  p->ell_decay = 0.9;
+  p->ell_min = 0.02;
+  p->schedule = CVO_SCHEDULE_DECAY;
+  p->sigma = 1.0;
+  p->kcut = 1e-3;
+  p->color_mode = CVO_COLOR_KERNEL;
+  p->ell_color = 0.1;
+  p->color_scale = 1e-5;
+  p->a2 = 1.0;
+  p->b2 = 1.0;
+  p->max_iters = 200;
+  p->eps_pose = 1e-5;
+  p->eps_grad = 5e-5;
+  p->step_order = 4;
+  p->feat_dim = 5;
+  p->cell_factor = 1.0;
+}
+
+const char* cvo_strerror(int s) {
+  switch (s) {
+    case CVO_OK: return "CVO_OK";
+    case CVO_ERR_INVALID_ARG: return "CVO_ERR_INVALID_ARG";
+    case CVO_ERR_OUT_OF_BUDGET: return "CVO_ERR_OUT_OF_BUDGET";
+    case CVO_ERR_CUDA: return "CVO_ERR_CUDA";
+    case CVO_ERR_TIMEOUT: return "CVO_ERR_TIMEOUT";
+    case CVO_ERR_BUSY: return "CVO_ERR_BUSY";
+    case CVO_ERR_NOT_FOUND: return "CVO_ERR_NOT_FOUND";
+    case CVO_ERR_INTERNAL: return "CVO_ERR_INTERNAL";
+    default: return "CVO_ERR_UNKNOWN";
+  }
+}
+
+const char* cvo_last_error(cvo_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cvo_ctx** out) {
+  if (!out) return CVO_ERR_INVALID_ARG;
+  *out = nullptr;
+  cvo_params p;
+  if (params) p = *params;
+  else cvo_params_default(&p);
+  const bool ok = p.ell0 > 0 && p.ell_min > 0 && p.ell_decay > 0 && p.ell_decay <= 1 &&
+                  p.sigma > 0 && p.kcut > 0 && p.kcut < 1 && p.a2 > 0 && p.b2 > 0 &&
+                  p.max_iters >= 0 && p.max_iters <= 100000 && p.feat_dim >= 0 &&
+                  p.feat_dim <= CVO_MAX_FEAT && (p.step_order == 2 || p.step_order == 4) &&
+                  (p.schedule == CVO_SCHEDULE_DECAY || p.schedule == CVO_SCHEDULE_TABLE1) &&
+                  (p.color_mode >= CVO_COLOR_NONE && p.color_mode <= CVO_COLOR_DOT) &&
+                  (p.color_mode != CVO_COLOR_KERNEL || p.ell_color > 0) &&
+                  (p.color_mode != CVO_COLOR_DOT || p.color_scale > 0) &&
+                  p.cell_factor >= 0.5 && p.cell_factor <= 8.0 && std::isfinite(p.ell0);
+  if (!ok) return CVO_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return CVO_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return CVO_ERR_CUDA;
+  cvo_ctx* ctx = new cvo_ctx();
+  ctx->device = device;
+  ctx->prm = p;
+  if (p.feat_dim == 0) ctx->prm.color_mode = CVO_COLOR_NONE;
+  ctx->budget = hbm_budget_bytes;
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_state, sizeof(SolveState)) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_stats, sizeof(CloudStats)) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_int, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->d_stats, sizeof(CloudStats)) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cvo_destroy(ctx);
+    return CVO_ERR_CUDA;
+  }
+  *out = ctx;
+  return CVO_OK;
+}
+
+int cvo_destroy(cvo_ctx* ctx) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->plans) free_plan(ctx, kv.second);
+  ctx->plans.clear();
+  free_plan(ctx, ctx->eval_plan);
+  for (Cloud* c : ctx->clouds) free_cloud(ctx, c);
+  ctx->clouds.clear();
+  if (ctx->d_stats) cudaFree(ctx->d_stats);
+  if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
+  if (ctx->h_int) cudaFreeHost(ctx->h_int);
+  if (ctx->h_state) cudaFreeHost(ctx->h_state);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return CVO_OK;
+}
+
+int cvo_set_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, uint32_t flags,
+                  void* stream, int32_t* handle_out) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!xyz || !handle_out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL xyz or handle pointer");
+  if (n <= 0 || n > kMaxPoints) return fail(ctx, CVO_ERR_INVALID_ARG, "point count out of range");
+  const int D = ctx->prm.color_mode == CVO_COLOR_NONE ? 0 : ctx->prm.feat_dim;
+  if (D > 0 && !feat) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL feature pointer");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t us = stream ? (cudaStream_t)stream : ctx->stream;
+  Cloud* c = new Cloud();
+  c->n = n;
+  c->n_pad = (int)((n + 31) / 32 * 32);
+  c->D = D;
+  c->dp = padded_dim(ctx->prm);
+  const bool on_dev = (flags & CVO_DEVICE_PTR) != 0;
+  float *raw_xyz = nullptr, *raw_feat = nullptr;
+  int rc = CVO_OK;
+  auto cleanup = [&](int code) {
+    if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
+    if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    free_cloud(ctx, c);
+    return code;
+  };
+  // staging copy of the raw input (library-owned)
+  cudaError_t e = cudaMallocAsync((void**)&raw_xyz, sizeof(float) * 3 * n, ctx->stream);
+  if (e == cudaSuccess && D > 0)
+    e = cudaMallocAsync((void**)&raw_feat, sizeof(float) * D * n, ctx->stream);
+  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  if (on_dev && us != ctx->stream) {
+    // order the caller's stream before our copies
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, us);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  }
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  e = cudaMemcpyAsync(raw_xyz, xyz, sizeof(float) * 3 * n, kind, ctx->stream);
+  if (e == cudaSuccess && D > 0)
+    e = cudaMemcpyAsync(raw_feat, feat, sizeof(float) * D * n, kind, ctx->stream);
+  if (e == cudaSuccess) e = cloud_stats(raw_xyz, raw_feat, (int)n, D, ctx->d_stats, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(CloudStats), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  const CloudStats st = *ctx->h_stats;
+  if (st.bad) return cleanup(fail(ctx, CVO_ERR_INVALID_ARG, "cloud has a non-finite value"));
+  for (int a = 0; a < 3; ++a) {
+    c->c[a] = st.sum[a] / (double)n;
+    // bounding box in the centred frame, widened by a few ulps
+    const double lo = (double)st.lo[a] - c->c[a], hi = (double)st.hi[a] - c->c[a];
+    const double pad = 1e-6 * (1.0 + std::fabs(lo) + std::fabs(hi));
+    c->lo[a] = (float)(lo - pad);
+    c->hi[a] = (float)(hi + pad);
+  }
+  c->mf = morton_frame(c->lo, c->hi);
+  rc = dev_alloc(ctx, (void**)&c->xyz, sizeof(float4) * c->n_pad, &c->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&c->zs, sizeof(float4) * c->n_pad, &c->bytes);
+  if (rc == CVO_OK && c->dp > 0)
+    rc = dev_alloc(ctx, (void**)&c->feat, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
+  if (rc == CVO_OK && c->dp > 0)
+    rc = dev_alloc(ctx, (void**)&c->zf, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
+  if (rc != CVO_OK) return cleanup(rc);
+  e = pack_cloud(raw_xyz, raw_feat, (int)n, D, c->dp, c->n_pad, c->c[0], c->c[1], c->c[2],
+                 feature_scale(ctx->prm), c->xyz, c->feat, ctx->stream);
+  if (e == cudaSuccess)
+    e = morton_order(c->xyz, c->feat, (int)n, c->dp, c->n_pad, c->mf, c->zs, c->zf, ctx->stream);
+  if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
+  if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
+  raw_xyz = raw_feat = nullptr;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  // reuse a free slot
+  int32_t h = -1;
+  for (size_t i = 0; i < ctx->clouds.size(); ++i)
+    if (!ctx->clouds[i]) {
+      h = (int32_t)i;
+      break;
+    }
+  if (h < 0) {
+    h = (int32_t)ctx->clouds.size();
+    ctx->clouds.push_back(nullptr);
+  }
+  ctx->clouds[h] = c;
+  *handle_out = h;
+  return CVO_OK;
+}
+
+int cvo_release_cloud(cvo_ctx* ctx, int32_t handle) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Cloud* c = get_cloud(ctx, handle);
+  if (!c) return fail(ctx, CVO_ERR_NOT_FOUND, "unknown cloud handle");
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+    if (it->first.first == handle || it->first.second == handle) {
+      free_plan(ctx, it->second);
+      it = ctx->plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  free_cloud(ctx, c);
+  ctx->clouds[handle] = nullptr;
+  return CVO_OK;
+}
+
+int cvo_eval(cvo_ctx* ctx, int32_t target, int32_t source, const double P[16], double ell,
+             cvo_eval_result* out) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Cloud* t = get_cloud(ctx, target);
+  Cloud* s = get_cloud(ctx, source);
+  if (!t || !s) return fail(ctx, CVO_ERR_NOT_FOUND, "unknown cloud handle");
+  if (!out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL result pointer");
+  if (!(ell > 0) || !std::isfinite(ell)) return fail(ctx, CVO_ERR_INVALID_ARG, "ell must be > 0");
+  int rc = check_pose(ctx, P);
+  if (rc != CVO_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  if (!ctx->eval_plan) ctx->eval_plan = new Plan();
+  Plan* p = ctx->eval_plan;
+  rc = configure_plan(ctx, p, t, s, std::vector<double>(1, ell), kModeEval);
+  if (rc != CVO_OK) return rc;
+  SolveState* hs = ctx->h_state;
+  std::memset(hs, 0, sizeof(SolveState));
+  std::memcpy(hs->P0, P, sizeof(double) * 16);
+  CK(cudaMemcpyAsync(p->d_state, hs, offsetof(SolveState, P), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(launch_init(p->d_cfg, p->d_state, 0, 0, ctx->stream));
+  CK(launch_iteration(p, 0, 0, ctx->stream));
+  CK(cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hs->status != 0) return fail(ctx, CVO_ERR_INTERNAL, "cell-row segment overflow");
+  out->F = hs->F;
+  for (int a = 0; a < 6; ++a) out->grad6[a] = hs->xi[a];
+  for (int m = 0; m < 5; ++m) out->S[m] = hs->S[m];
+  out->nnz = (int64_t)hs->nnz_eval;
+  out->candidates = (int64_t)hs->cand_eval;
+  return CVO_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Look up (or build) the solve plan of (target, source) and stage P0.
+int prepare_solve(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
+                  double P_out[16], Plan** out) {
+  Cloud* t = get_cloud(ctx, target);
+  Cloud* s = get_cloud(ctx, source);
+  if (!t || !s) return fail(ctx, CVO_ERR_NOT_FOUND, "unknown cloud handle");
+  if (!P_out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL output pose");
+  int rc = check_pose(ctx, P0);
+  if (rc != CVO_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  auto key = std::make_pair((int)target, (int)source);
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) {
+    p = it->second;
+  } else {
+    rc = build_plan(ctx, target, source, &p);
+    if (rc != CVO_OK) return rc;
+    ctx->plans[key] = p;
+  }
+  SolveState* hs = ctx->h_state;
+  std::memset(hs, 0, offsetof(SolveState, P));
+  std::memcpy(hs->P0, P0, sizeof(double) * 16);
+  CK(cudaMemcpyAsync(p->d_state, hs, offsetof(SolveState, P), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  *out = p;
+  return CVO_OK;
+}
+
+void fill_stats(const SolveState* hs, cvo_stats* stats) {
+  if (stats) {
+    stats->iters = hs->iter;
+    stats->converged = hs->converged;
+    stats->fallback_steps = hs->fallback_steps;
+    stats->no_ascent_steps = hs->no_ascent_steps;
+    stats->final_ell = hs->ell;
+    stats->F_last = hs->F;
+    stats->t_last = hs->t;
+    stats->pair_evals = (int64_t)hs->nnz_total;
+    stats->candidates = (int64_t)hs->cand_total;
+    stats->status = hs->status;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int cvo_align(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16], double P_out[16],
+              cvo_stats* stats) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Plan* p = nullptr;
+  int rc = prepare_solve(ctx, target, source, P0, P_out, &p);
+  if (rc != CVO_OK) return rc;
+  SolveState* hs = ctx->h_state;
+  CK(cudaGraphLaunch(p->exec, ctx->stream));
+  CK(cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(P_out, hs->P, sizeof(double) * 16);
+  fill_stats(hs, stats);
+  if (hs->status != 0) return fail(ctx, CVO_ERR_INTERNAL, "cell-row segment overflow");
+  return CVO_OK;
+}
+
+int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
+                      double P_out[16], cvo_stats* stats, cvo_iter_profile* records,
+                      int max_records, int* n_records) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (max_records > 0 && !records) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL records");
+  Plan* p = nullptr;
+  int rc = prepare_solve(ctx, target, source, P0, P_out, &p);
+  if (rc != CVO_OK) return rc;
+  Cloud* s = get_cloud(ctx, source);
+  SolveState* hs = ctx->h_state;
+  const std::vector<double> ells = ell_schedule(ctx->prm, std::max(1, ctx->prm.max_iters));
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  auto destroy = [&]() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  int nrec = 0;
+  cudaError_t e = launch_init(p->d_cfg, p->d_state, 0, 0, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  unsigned long long prev_total = 0;
+  for (int k = 0; e == cudaSuccess && !hs->done && k < ctx->prm.max_iters; ++k) {
+    // a short device-side delay lets the host enqueue the whole iteration
+    // before the first event fires, so the events time kernels, not launches
+    e = launch_delay(30000, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], ctx->stream);
+    if (e == cudaSuccess) e = launch_plan(p->d_cfg, p->d_state, p->ncl_launch, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_pair_pass(false, s->dp, ctx->prm.color_mode, p->nblocks, p->d_cfg, p->d_state,
+                           p->d_partials, 0, 0, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_pair_pass(true, s->dp, ctx->prm.color_mode, p->nblocks, p->d_cfg, p->d_state,
+                           p->d_partials, 0, 0, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) break;
+    if (nrec < max_records) {
+      cvo_iter_profile& r = records[nrec++];
+      r.ell = ells[std::min<size_t>(k, ells.size() - 1)];
+      cudaEventElapsedTime(&r.plan_ms, ev[0], ev[1]);
+      cudaEventElapsedTime(&r.grad_ms, ev[1], ev[2]);
+      cudaEventElapsedTime(&r.step_ms, ev[2], ev[3]);
+      const unsigned long long pass_total = hs->nnz_total - prev_total;
+      r.grad_pairs = (int64_t)hs->nnz_eval;
+      r.step_pairs = (int64_t)(pass_total - hs->nnz_eval);
+      r.grad_candidates = (int64_t)hs->cand_eval;
+      r.step_candidates = 0;
+    }
+    prev_total = hs->nnz_total;
+  }
+  destroy();
+  if (e != cudaSuccess) return fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e));
+  // the step pass visits exactly the candidates of the gradient pass
+  for (int i = 0; i < nrec; ++i) records[i].step_candidates = records[i].grad_candidates;
+  if (n_records) *n_records = nrec;
+  std::memcpy(P_out, hs->P, sizeof(double) * 16);
+  fill_stats(hs, stats);
+  if (hs->status != 0) return fail(ctx, CVO_ERR_INTERNAL, "cell-row segment overflow");
+  return CVO_OK;
+}
+
+void* cvo_stream(cvo_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal types shared by the CUDA translation units of libcvo.
+//
+// Frames: every cloud is stored centred on its own FP64 centroid (target
+// centroid cX, source centroid cZ) so that FP32 pair arithmetic never
+// subtracts two large coordinates. A source point z' (centred) is mapped into
+// the target's centred frame by z~' = R z' + T' with T' = R cZ + T - cX; the
+// gradient is mapped back to the frame P acts in by omega = omega' + cX x v
+// (exact, since z~ = z~' + cX).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cvo {
+
+constexpr int kWarps = 8;                 // warps per block of the pair passes
+constexpr int kThreads = kWarps * 32;     // threads per block
+constexpr int kMaxLevels = 8;             // target cell lists one solve may use
+constexpr int kMaxFeatPad = 8;            // padded feature planes (3, 5 or 8)
+constexpr int kMaxPoints = 1 << 22;       // largest cloud (keeps candidate counts in int32)
+constexpr int kMaxCells = 1 << 22;        // largest cell list
+constexpr int kPartialStride = 8;         // doubles per block partial
+constexpr int kClusterMax = 32;           // source points per cluster
+constexpr int kMaxSeg = 64;               // cell-row segments per cluster
+constexpr int kMortonBits = 10;           // Morton quantisation per axis
+
+enum : int { kColorNone = 0, kColorKernel = 1, kColorDot = 2 };
+enum : int { kModeAlign = 0, kModeEval = 1 };
+enum : int { kStatusSegOverflow = 1 };    // bit set in SolveState::status
+
+// One uniform-grid cell list over a target cloud (Sec. 5 sparsification:
+// only cells within the cutoff radius of a source point are visited).
+struct GridView {
+  const float4* xyz;       // n points sorted by cell (x fastest), centred; w unused
+  const float* feat;       // dp planes of n_pad floats, same order, pre-scaled
+  const int* cell_start;   // ncells + 1 offsets into xyz
+  int n, n_pad;
+  int nx, ny, nz;
+  float ox, oy, oz;        // origin of cell (0,0,0), centred frame
+  float h, inv_h;          // cell edge and its inverse
+};
+
+// Source points in Morton order, cut into spatially bounded clusters
+// (octree nodes of the source's own frame, at most kClusterMax points).
+struct ClusterView {
+  const int* cstart;       // ncl + 1 offsets into the Morton-ordered source
+  int ncl;
+};
+
+struct SourceView {
+  const float4* xyz;       // m points, Morton order, centred
+  const float* feat;       // dp planes of m_pad floats, pre-scaled
+  int m, m_pad;
+};
+
+// Constants of one iteration, precomputed on the host from the lengthscale.
+struct IterConst {
+  double ell;              // lengthscale
+  double inv_l2;           // 1 / ell^2
+  float A;                 // log2(e) / (2 ell^2)
+  float rc2;               // cutoff radius squared
+  float rprune;            // traversal radius (r_c widened by 1e-3 relative)
+  int level;               // grid / cluster level
+};
+
+// Constant for one solve plan (device memory).
+struct SolveCfg {
+  GridView grids[kMaxLevels];
+  ClusterView clusters[kMaxLevels];
+  SourceView src;
+  const IterConst* iters;  // one entry per iteration (one in eval mode)
+  // per-iteration work buffers, sized for the largest level
+  float4* zt;              // transformed source points, m_pad
+  int* seg_xs;             // first target index of each segment, ncl_max * kMaxSeg
+  int* seg_pref;           // candidate offset of each segment in its cluster
+  int* cl_nseg;            // segments per cluster
+  int* cl_cand;            // candidates per cluster
+  int* chunk_pref;         // ncl_max + 1: exclusive prefix of 32-candidate chunks
+  int* warp_start;         // first cluster of each pair-pass warp
+  int nwarps;              // warps of a pair pass (= nblocks * kWarps)
+  int nblocks;             // blocks of a pair pass
+  double cX[3], cZ[3];     // FP64 centroids
+  double sigma2, a2, b2;
+  double ell_floor, eps_pose, eps_grad;
+  int max_iters, step_order, mode;
+  int pad0;
+};
+
+// Mutable state of one solve (device memory). The host writes the input
+// block (P0) before a launch and reads the rest after.
+struct SolveState {
+  // inputs
+  double P0[16];
+  // pose and last pass results
+  double P[16];
+  double xi[6];              // metric gradient at P
+  double xi_norm;
+  double F;                  // F at P (gradient pass)
+  double S[5];               // step sums along xi
+  double t, t_prev;
+  double ell;                // lengthscale of the current iteration
+  int level;                 // level of the current iteration
+  int iter, done, converged;
+  int fallback_steps, no_ascent_steps, have_t_prev, status;
+  unsigned long long nnz_total, cand_total;
+  unsigned long long nnz_pass[2], cand_pass[2];
+  unsigned long long nnz_eval, cand_eval;   // gradient pass of the last iteration
+  unsigned int ticket[2];
+  // FP32 constants of the current iteration (centred frames)
+  float R[9], T[3];          // z~' = R z' + T
+  float om[3], vc[3];        // unit step direction: omega, v + omega x cX
+  float A, rc2, rprune, inv_l2f;
+};
+
+// ---- grid.cu --------------------------------------------------------------
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int n, int bits,
+                             cudaStream_t s);
+
+struct CloudStats {
+  double sum[3];
+  float lo[3], hi[3];
+  int bad;
+  int pad;
+};
+// FP64 sum, FP32 bounding box and a non-finite check of a raw cloud.
+cudaError_t cloud_stats(const float* xyz, const float* feat, int n, int D,
+                        CloudStats* d_out, cudaStream_t s);
+
+// Centre, pack (float4 xyz) and pre-scale features into dp SoA planes.
+cudaError_t pack_cloud(const float* xyz, const float* feat, int n, int D, int dp, int n_pad,
+                       double cx, double cy, double cz, float feat_scale,
+                       float4* out_xyz, float* out_feat, cudaStream_t s);
+
+// Morton quantisation shared by the source ordering and its clusters.
+struct MortonFrame {
+  float lo[3];
+  float scale;             // quantisation cells per metre
+  float cell;              // edge of one quantisation cell
+};
+MortonFrame morton_frame(const float lo[3], const float hi[3]);
+
+// Reorder a packed cloud along a Morton curve of its bounding box.
+cudaError_t morton_order(const float4* xyz, const float* feat, int n, int dp, int n_pad,
+                         const MortonFrame& mf, float4* out_xyz, float* out_feat,
+                         cudaStream_t s);
+
+// Cut a Morton-ordered cloud into clusters: runs sharing the Morton prefix of
+// an octree node with edge <= max_edge, split into runs of <= kClusterMax.
+// cstart receives ncl + 1 offsets (capacity n + 1); *d_ncl the count.
+cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, float max_edge,
+                           int* cstart, int* d_ncl, cudaStream_t s);
+
+// Build a cell list of edge h over a packed cloud.
+cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int n_pad,
+                       int nx, int ny, int nz, float ox, float oy, float oz, float h,
+                       float4* out_xyz, float* out_feat, int* cell_start, cudaStream_t s);
+
+// ---- pair_kernels.cu -------------------------------------------------------
+// The kernels of one solve iteration: init (once), then plan, chunk split,
+// gradient pass and step pass. ncl_launch: largest cluster count of any level.
+cudaError_t launch_delay(unsigned ns, cudaStream_t s);
+cudaError_t launch_init(const SolveCfg* cfg, SolveState* st, cudaGraphConditionalHandle cond,
+                        int use_cond, cudaStream_t s);
+cudaError_t launch_plan(const SolveCfg* cfg, SolveState* st, int ncl_launch, cudaStream_t s);
+cudaError_t launch_pair_pass(bool step, int dp, int color_mode, int nblocks,
+                             const SolveCfg* cfg, SolveState* st, double* partials,
+                             cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+
+}  // namespace cvo
