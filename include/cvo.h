@@ -83,7 +83,13 @@ typedef struct {
     double eps_grad;    /* ... or when |xi| < eps_grad there; 5e-5 (Table 1) */
     int step_order;     /* 4: first maximiser of the quartic Taylor model (Eq. fourth); 2: quadratic */
     int feat_dim;       /* feature dimension D in [0, CVO_MAX_FEAT]; 5. 0 forces COLOR_NONE */
-    double cell_factor; /* cell edge of the target grid as a multiple of the cutoff radius; 1.0 */
+    double cell_factor; /* cell edge of the target grid as a multiple of the cutoff radius, in
+                           [0.5, 8]; 0.7. Performance only: the cutoff test is exact. */
+    /* performance tuning (results do not depend on these): */
+    double cluster_factor; /* source cluster (octree node) edge as a multiple of the cell edge,
+                              capped so a cluster spans at most 8 x 8 cell rows; 2.0 */
+    int cost_chunk;        /* work split: per-chunk overhead in pair-test units; 24 */
+    int cost_cluster;      /* work split: cost of staging one cluster in pair-test units; 64 */
 } cvo_params;
 
 /* One evaluation at a fixed pose (cvo_eval). */
@@ -144,29 +150,34 @@ int cvo_eval(cvo_ctx* ctx, int32_t target, int32_t source, const double P[16], d
 
 /* Full solve from P0 (Problem 1; Eqs. flow, fourth, newstep, step): gradient,
  * step sums, quartic step and exponential-map update per iteration, with the
- * lengthscale schedule of the context. The whole loop runs on the device as
- * one CUDA graph with a device-side while loop. Synchronous. P_out receives
- * the final pose; stats (may be NULL) the solve statistics. */
+ * lengthscale schedule of the context. The whole loop runs on the device in
+ * one persistent cooperative kernel launch. Synchronous. P_out receives the
+ * final pose; stats (may be NULL) the solve statistics. Returns
+ * CVO_ERR_TIMEOUT if a bounded device-side barrier wait expired. */
 int cvo_align(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
               double P_out[16], cvo_stats* stats);
 
 /* Per-iteration record of cvo_align_profile. */
 typedef struct {
     double ell;               /* lengthscale of the iteration */
-    float plan_ms;            /* CUDA-event duration of the traversal plan (cell rows per cluster) */
-    float grad_ms, step_ms;   /* CUDA-event durations of the gradient and step pair passes */
+    float plan_ms;            /* time spent rebuilding the traversal plan (0 when it was reused) */
+    float grad_ms;            /* gradient pass, including its FP64 reduction and tail */
+    float step_ms;            /* step pass, including the step length and pose update */
+    float grad_pass_ms;       /* part of grad_ms before the barrier that ends the pass (first block) */
+    float grad_sync_ms;       /* part of grad_ms up to the end of that barrier */
+    float step_pass_ms;       /* the same two points for the step pass */
+    float step_sync_ms;
+    int replanned;            /* 1 if the traversal plan was rebuilt in this iteration */
     int64_t grad_pairs;       /* pairs kept in the gradient pass */
     int64_t step_pairs;       /* pairs kept in the step pass */
     int64_t grad_candidates;  /* candidates visited in the gradient pass */
     int64_t step_candidates;  /* candidates visited in the step pass */
 } cvo_iter_profile;
 
-/* The same solve as cvo_align (same plan, kernels and results) with the
- * iteration loop driven from the host instead of the device-side graph loop,
- * so that each pair pass can be bracketed by CUDA events on the context
- * stream. Slower than cvo_align (one host round trip per iteration); meant
- * for measurement. Writes min(iters, max_records) records and the count to
- * *n_records (may be NULL). */
+/* The same solve as cvo_align (same kernel and results) with per-iteration
+ * phase timings, taken on the device from the global nanosecond timer by the
+ * first block of the solve kernel. Writes min(iters, max_records) records and
+ * the count to *n_records (may be NULL). */
 int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
                       double P_out[16], cvo_stats* stats, cvo_iter_profile* records,
                       int max_records, int* n_records);

@@ -60,7 +60,8 @@ class cvo_params(ctypes.Structure):
                 ("b2", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("eps_pose", ctypes.c_double), ("eps_grad", ctypes.c_double),
                 ("step_order", ctypes.c_int), ("feat_dim", ctypes.c_int),
-                ("cell_factor", ctypes.c_double)]
+                ("cell_factor", ctypes.c_double), ("cluster_factor", ctypes.c_double),
+                ("cost_chunk", ctypes.c_int), ("cost_cluster", ctypes.c_int)]
 
 
 class cvo_eval_result(ctypes.Structure):
@@ -79,7 +80,10 @@ class cvo_stats(ctypes.Structure):
 
 class cvo_iter_profile(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_double), ("plan_ms", ctypes.c_float), ("grad_ms", ctypes.c_float),
-                ("step_ms", ctypes.c_float), ("grad_pairs", ctypes.c_int64),
+                ("step_ms", ctypes.c_float), ("grad_pass_ms", ctypes.c_float),
+                ("grad_sync_ms", ctypes.c_float), ("step_pass_ms", ctypes.c_float),
+                ("step_sync_ms", ctypes.c_float), ("replanned", ctypes.c_int),
+                ("grad_pairs", ctypes.c_int64),
                 ("step_pairs", ctypes.c_int64), ("grad_candidates", ctypes.c_int64),
                 ("step_candidates", ctypes.c_int64)]
 

@@ -47,8 +47,9 @@ struct Cloud {
   MortonFrame mf{};
   float4* xyz = nullptr;  // packed, original order
   float* feat = nullptr;
-  float4* zs = nullptr;   // Morton order (source role)
+  float4* zs = nullptr;   // Morton order (source role, and input of the cell lists)
   float* zf = nullptr;
+  double radius = 0.0;    // max |x'| over the centred cloud (from its bounding box)
   std::vector<Grid> grids;
   std::vector<Clusters> clusters;
   size_t bytes = 0;
@@ -61,21 +62,16 @@ struct Plan {
   IterConst* d_iters = nullptr;
   SolveState* d_state = nullptr;
   double* d_partials = nullptr;
-  float4* zt = nullptr;
+  IterRecord* d_records = nullptr;
   int* seg_xs = nullptr;
   int* seg_pref = nullptr;
   int* cl_nseg = nullptr;
   int* cl_cand = nullptr;
-  int* chunk_pref = nullptr;
-  int* warp_start = nullptr;
-  int cap_iters = 0, cap_ncl = 0, cap_m_pad = 0;
+  long long* group_agg = nullptr;
+  int cap_iters = 0, cap_ncl = 0;
   int nblocks = 0;
-  int ncl_launch = 0;
   int n_iters = 0;
   int dp = 0, color_mode = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphConditionalHandle cond = 0;
   size_t bytes = 0;
 };
 
@@ -167,28 +163,26 @@ void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
   cudaFree(p->d_iters);
   cudaFree(p->d_state);
   cudaFree(p->d_partials);
-  cudaFree(p->zt);
+  cudaFree(p->d_records);
   cudaFree(p->seg_xs);
   cudaFree(p->seg_pref);
   cudaFree(p->cl_nseg);
   cudaFree(p->cl_cand);
-  cudaFree(p->chunk_pref);
-  cudaFree(p->warp_start);
+  cudaFree(p->group_agg);
   release_bytes(ctx, p->bytes);
   p->d_cfg = nullptr;
   p->d_iters = nullptr;
   p->d_state = nullptr;
   p->d_partials = nullptr;
-  p->zt = nullptr;
-  p->seg_xs = p->seg_pref = p->cl_nseg = p->cl_cand = p->chunk_pref = p->warp_start = nullptr;
+  p->d_records = nullptr;
+  p->seg_xs = p->seg_pref = p->cl_nseg = p->cl_cand = nullptr;
+  p->group_agg = nullptr;
   p->bytes = 0;
-  p->cap_iters = p->cap_ncl = p->cap_m_pad = 0;
+  p->cap_iters = p->cap_ncl = 0;
 }
 
 void free_plan(cvo_ctx* ctx, Plan* p) {
   if (!p) return;
-  if (p->exec) cudaGraphExecDestroy(p->exec);
-  if (p->graph) cudaGraphDestroy(p->graph);
   free_plan_buffers(ctx, p);
   delete p;
 }
@@ -237,7 +231,9 @@ int ensure_grid(cvo_ctx* ctx, Cloud* c, double h_req, int* index_out) {
     return rc;
   }
   const float hf = (float)h;
-  cudaError_t e = build_grid(c->xyz, c->feat, n, c->dp, c->n_pad, nx, ny, nz, c->lo[0], c->lo[1],
+  // built from the Morton-ordered copy: the stable cell sort keeps each cell's
+  // points in Morton order, so consecutive candidates are spatially compact
+  cudaError_t e = build_grid(c->zs, c->zf, n, c->dp, c->n_pad, nx, ny, nz, c->lo[0], c->lo[1],
                              c->lo[2], hf, g.xyz, g.feat, g.cell_start, ctx->stream);
   if (e != cudaSuccess) {
     free_grid(ctx, g);
@@ -312,35 +308,32 @@ double ell_floor(const cvo_params& p) {
 }
 
 // Grow the plan's device buffers to the given capacities.
-int reserve_plan(cvo_ctx* ctx, Plan* p, int iters, int ncl, int m_pad, int nblocks) {
-  if (p->d_cfg && iters <= p->cap_iters && ncl <= p->cap_ncl && m_pad <= p->cap_m_pad &&
-      nblocks == p->nblocks)
+int reserve_plan(cvo_ctx* ctx, Plan* p, int iters, int ncl, int nblocks) {
+  if (p->d_cfg && iters <= p->cap_iters && ncl <= p->cap_ncl && nblocks == p->nblocks)
     return CVO_OK;
   free_plan_buffers(ctx, p);
   iters = std::max(iters, 1);
   ncl = std::max(ncl, 1);
+  const int ng = (ncl + 31) / 32;
   int rc = dev_alloc(ctx, (void**)&p->d_cfg, sizeof(SolveCfg), &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->d_iters, sizeof(IterConst) * iters, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->d_state, sizeof(SolveState), &p->bytes);
   if (rc == CVO_OK)
-    rc = dev_alloc(ctx, (void**)&p->d_partials, sizeof(double) * kPartialStride * nblocks, &p->bytes);
-  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->zt, sizeof(float4) * m_pad, &p->bytes);
+    rc = dev_alloc(ctx, (void**)&p->d_partials, sizeof(double) * 2 * kPartialStride * nblocks,
+                   &p->bytes);
+  if (rc == CVO_OK)
+    rc = dev_alloc(ctx, (void**)&p->d_records, sizeof(IterRecord) * iters, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->seg_xs, sizeof(int) * (size_t)ncl * kMaxSeg, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->seg_pref, sizeof(int) * (size_t)ncl * kMaxSeg, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_nseg, sizeof(int) * ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_cand, sizeof(int) * ncl, &p->bytes);
-  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->chunk_pref, sizeof(int) * (ncl + 1), &p->bytes);
-  if (rc == CVO_OK)
-    rc = dev_alloc(ctx, (void**)&p->warp_start, sizeof(int) * nblocks * kWarps, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->group_agg, sizeof(long long) * ng, &p->bytes);
   if (rc != CVO_OK) {
     free_plan_buffers(ctx, p);
     return rc;
   }
-  cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(SolveState), ctx->stream);
-  if (e != cudaSuccess) return fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e));
   p->cap_iters = iters;
   p->cap_ncl = ncl;
-  p->cap_m_pad = m_pad;
   p->nblocks = nblocks;
   return CVO_OK;
 }
@@ -371,14 +364,22 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
     int rc = ensure_grid(ctx, t, hs[l], &gi);
     if (rc != CVO_OK) return rc;
     cfg.grids[l] = t->grids[gi].view;
-    rc = ensure_clusters(ctx, s, 0.5f * t->grids[gi].view.h, &ki);
+    // cluster edge: cluster_factor cells, capped so that the cluster's rotated
+    // bounding box widened by the plan radius (<= 2.21 r_c) spans <= 6 cells,
+    // i.e. at most 8 x 8 = kMaxSeg cell rows
+    const double hh = t->grids[gi].view.h;
+    const double rc_level = hs[l] / f;
+    const double edge = std::min(prm.cluster_factor * hh, (6.0 * hh - 2.21 * rc_level) / std::sqrt(3.0));
+    rc = ensure_clusters(ctx, s, (float)edge, &ki);
     if (rc != CVO_OK) return rc;
     cfg.clusters[l].cstart = s->clusters[ki].cstart;
     cfg.clusters[l].ncl = s->clusters[ki].ncl;
     ncl_max = std::max(ncl_max, s->clusters[ki].ncl);
   }
-  const int nblocks = 2 * ctx->sms;
-  int rc = reserve_plan(ctx, p, (int)ells.size(), ncl_max, s->n_pad, nblocks);
+  const int per_sm = solve_blocks_per_sm(s->dp, prm.color_mode);
+  if (per_sm <= 0) return fail(ctx, CVO_ERR_CUDA, "solve kernel cannot be resident");
+  const int nblocks = std::min(per_sm * ctx->sms, 512);   // the tail reduction covers 512
+  int rc = reserve_plan(ctx, p, (int)ells.size(), ncl_max, nblocks);
   if (rc != CVO_OK) return rc;
   std::vector<IterConst> ic(ells.size());
   const double log2e = 1.4426950408889634073599246810019;
@@ -397,15 +398,14 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   cfg.src.m = (int)s->n;
   cfg.src.m_pad = s->n_pad;
   cfg.iters = p->d_iters;
-  cfg.zt = p->zt;
   cfg.seg_xs = p->seg_xs;
   cfg.seg_pref = p->seg_pref;
   cfg.cl_nseg = p->cl_nseg;
   cfg.cl_cand = p->cl_cand;
-  cfg.chunk_pref = p->chunk_pref;
-  cfg.warp_start = p->warp_start;
-  cfg.nblocks = nblocks;
-  cfg.nwarps = nblocks * kWarps;
+  cfg.group_agg = p->group_agg;
+  cfg.src_radius = s->radius;
+  cfg.cost_chunk = prm.cost_chunk;
+  cfg.cost_cluster = prm.cost_cluster;
   for (int a = 0; a < 3; ++a) {
     cfg.cX[a] = t->c[a];
     cfg.cZ[a] = s->c[a];
@@ -424,24 +424,10 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
                      ctx->stream));
   CK(cudaMemcpyAsync(p->d_cfg, &cfg, sizeof(SolveCfg), cudaMemcpyHostToDevice, ctx->stream));
   p->h_cfg = cfg;
-  p->ncl_launch = ncl_max;
   p->n_iters = (int)ells.size();
   p->dp = s->dp;
   p->color_mode = prm.color_mode;
   return CVO_OK;
-}
-
-// Kernels of one iteration body on stream s.
-cudaError_t launch_iteration(Plan* p, cudaGraphConditionalHandle cond, int use_cond,
-                             cudaStream_t s) {
-  cudaError_t e = launch_plan(p->d_cfg, p->d_state, p->ncl_launch, s);
-  if (e == cudaSuccess)
-    e = launch_pair_pass(false, p->dp, p->color_mode, p->nblocks, p->d_cfg, p->d_state,
-                         p->d_partials, cond, use_cond, s);
-  if (e == cudaSuccess)
-    e = launch_pair_pass(true, p->dp, p->color_mode, p->nblocks, p->d_cfg, p->d_state,
-                         p->d_partials, cond, use_cond, s);
-  return e;
 }
 
 int build_plan(cvo_ctx* ctx, int tgt, int src, Plan** out) {
@@ -453,52 +439,27 @@ int build_plan(cvo_ctx* ctx, int tgt, int src, Plan** out) {
   const int max_iters = std::max(0, ctx->prm.max_iters);
   std::vector<double> ells = ell_schedule(ctx->prm, std::max(1, max_iters));
   int rc = configure_plan(ctx, p, t, s, ells, kModeAlign);
-  cudaError_t e = cudaSuccess;
-  if (rc == CVO_OK) e = cudaStreamSynchronize(ctx->stream);
-  // graph: init -> while(cond) { plan -> gradient pass -> step pass }
-  if (rc == CVO_OK && e == cudaSuccess) e = cudaGraphCreate(&p->graph, 0);
-  if (rc == CVO_OK && e == cudaSuccess)
-    e = cudaGraphConditionalHandleCreate(&p->cond, p->graph, 1, cudaGraphCondAssignDefault);
-  cudaGraph_t captured = nullptr;
-  if (rc == CVO_OK && e == cudaSuccess)
-    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, p->graph, nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal);
-  if (rc == CVO_OK && e == cudaSuccess) {
-    cudaError_t el = launch_init(p->d_cfg, p->d_state, p->cond, 1, ctx->cap_stream);
-    e = cudaStreamEndCapture(ctx->cap_stream, &captured);
-    if (e == cudaSuccess) e = el;
-  }
-  cudaGraphNode_t cnode;
-  cudaGraphNodeParams cp{};
-  if (rc == CVO_OK && e == cudaSuccess) {
-    size_t nnodes = 0;
-    e = cudaGraphGetNodes(p->graph, nullptr, &nnodes);
-    std::vector<cudaGraphNode_t> nodes(nnodes);
-    if (e == cudaSuccess) e = cudaGraphGetNodes(p->graph, nodes.data(), &nnodes);
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = p->cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, p->graph, nodes.data(), nullptr, nnodes, &cp);
-  }
-  if (rc == CVO_OK && e == cudaSuccess) {
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t el = launch_iteration(p, p->cond, 1, ctx->cap_stream);
-      e = cudaStreamEndCapture(ctx->cap_stream, &captured);
-      if (e == cudaSuccess) e = el;
-    }
-  }
-  if (rc == CVO_OK && e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
-  if (rc == CVO_OK && e != cudaSuccess)
-    rc = fail(ctx, CVO_ERR_CUDA, std::string("solve graph: ") + cudaGetErrorString(e));
   if (rc != CVO_OK) {
     free_plan(ctx, p);
     return rc;
   }
   *out = p;
+  return CVO_OK;
+}
+
+// Stage P0 (and a zeroed state, which also resets the grid barrier) and run
+// the solve kernel.
+int run_solve(cvo_ctx* ctx, Plan* p, const double P0[16], bool records) {
+  SolveState* hs = ctx->h_state;
+  std::memset(hs, 0, sizeof(SolveState));
+  std::memcpy(hs->P0, P0, sizeof(double) * 16);
+  CK(cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_solve(p->dp, p->color_mode, p->nblocks, p->d_cfg, p->d_state, p->d_partials,
+                  records ? p->d_records : nullptr, ctx->stream));
+  CK(cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hs->status & kStatusTimeout) return fail(ctx, CVO_ERR_TIMEOUT, "grid barrier timed out");
+  if (hs->status != 0) return fail(ctx, CVO_ERR_INTERNAL, "cell-row segment overflow");
   return CVO_OK;
 }
 
@@ -532,7 +493,10 @@ void cvo_params_default(cvo_params* p) {
   p->eps_grad = 5e-5;
   p->step_order = 4;
   p->feat_dim = 5;
-  p->cell_factor = 1.0;
+  p->cell_factor = 0.7;
+  p->cluster_factor = 2.0;
+  p->cost_chunk = 24;
+  p->cost_cluster = 64;
 }
 
 const char* cvo_strerror(int s) {
@@ -565,7 +529,9 @@ int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cv
                   (p.color_mode >= CVO_COLOR_NONE && p.color_mode <= CVO_COLOR_DOT) &&
                   (p.color_mode != CVO_COLOR_KERNEL || p.ell_color > 0) &&
                   (p.color_mode != CVO_COLOR_DOT || p.color_scale > 0) &&
-                  p.cell_factor >= 0.5 && p.cell_factor <= 8.0 && std::isfinite(p.ell0);
+                  p.cell_factor >= 0.5 && p.cell_factor <= 8.0 && std::isfinite(p.ell0) &&
+                  p.cluster_factor > 0.0 && p.cluster_factor <= 8.0 && p.cost_chunk >= 0 &&
+                  p.cost_chunk <= 4096 && p.cost_cluster >= 0 && p.cost_cluster <= 65536;
   if (!ok) return CVO_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -669,6 +635,13 @@ int cvo_set_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, 
     c->hi[a] = (float)(hi + pad);
   }
   c->mf = morton_frame(c->lo, c->hi);
+  for (int cx = 0; cx < 2; ++cx)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cz = 0; cz < 2; ++cz) {
+        const double x = cx ? c->hi[0] : c->lo[0], y = cy ? c->hi[1] : c->lo[1],
+                     z = cz ? c->hi[2] : c->lo[2];
+        c->radius = std::max(c->radius, std::sqrt(x * x + y * y + z * z));
+      }
   rc = dev_alloc(ctx, (void**)&c->xyz, sizeof(float4) * c->n_pad, &c->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&c->zs, sizeof(float4) * c->n_pad, &c->bytes);
   if (rc == CVO_OK && c->dp > 0)
@@ -737,16 +710,9 @@ int cvo_eval(cvo_ctx* ctx, int32_t target, int32_t source, const double P[16], d
   Plan* p = ctx->eval_plan;
   rc = configure_plan(ctx, p, t, s, std::vector<double>(1, ell), kModeEval);
   if (rc != CVO_OK) return rc;
-  SolveState* hs = ctx->h_state;
-  std::memset(hs, 0, sizeof(SolveState));
-  std::memcpy(hs->P0, P, sizeof(double) * 16);
-  CK(cudaMemcpyAsync(p->d_state, hs, offsetof(SolveState, P), cudaMemcpyHostToDevice,
-                     ctx->stream));
-  CK(launch_init(p->d_cfg, p->d_state, 0, 0, ctx->stream));
-  CK(launch_iteration(p, 0, 0, ctx->stream));
-  CK(cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (hs->status != 0) return fail(ctx, CVO_ERR_INTERNAL, "cell-row segment overflow");
+  rc = run_solve(ctx, p, P, false);
+  if (rc != CVO_OK) return rc;
+  const SolveState* hs = ctx->h_state;
   out->F = hs->F;
   for (int a = 0; a < 6; ++a) out->grad6[a] = hs->xi[a];
   for (int m = 0; m < 5; ++m) out->S[m] = hs->S[m];
@@ -779,11 +745,6 @@ int prepare_solve(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[
     if (rc != CVO_OK) return rc;
     ctx->plans[key] = p;
   }
-  SolveState* hs = ctx->h_state;
-  std::memset(hs, 0, offsetof(SolveState, P));
-  std::memcpy(hs->P0, P0, sizeof(double) * 16);
-  CK(cudaMemcpyAsync(p->d_state, hs, offsetof(SolveState, P), cudaMemcpyHostToDevice,
-                     ctx->stream));
   *out = p;
   return CVO_OK;
 }
@@ -814,14 +775,12 @@ int cvo_align(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
   Plan* p = nullptr;
   int rc = prepare_solve(ctx, target, source, P0, P_out, &p);
   if (rc != CVO_OK) return rc;
-  SolveState* hs = ctx->h_state;
-  CK(cudaGraphLaunch(p->exec, ctx->stream));
-  CK(cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  rc = run_solve(ctx, p, P0, false);
+  const SolveState* hs = ctx->h_state;
   std::memcpy(P_out, hs->P, sizeof(double) * 16);
   fill_stats(hs, stats);
-  if (hs->status != 0) return fail(ctx, CVO_ERR_INTERNAL, "cell-row segment overflow");
-  return CVO_OK;
+  if (stats) stats->status = rc;
+  return rc;
 }
 
 int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
@@ -833,62 +792,34 @@ int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double
   Plan* p = nullptr;
   int rc = prepare_solve(ctx, target, source, P0, P_out, &p);
   if (rc != CVO_OK) return rc;
-  Cloud* s = get_cloud(ctx, source);
-  SolveState* hs = ctx->h_state;
-  const std::vector<double> ells = ell_schedule(ctx->prm, std::max(1, ctx->prm.max_iters));
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  for (auto& e : ev) CK(cudaEventCreate(&e));
-  auto destroy = [&]() {
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-  };
-  int nrec = 0;
-  cudaError_t e = launch_init(p->d_cfg, p->d_state, 0, 0, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  unsigned long long prev_total = 0;
-  for (int k = 0; e == cudaSuccess && !hs->done && k < ctx->prm.max_iters; ++k) {
-    // a short device-side delay lets the host enqueue the whole iteration
-    // before the first event fires, so the events time kernels, not launches
-    e = launch_delay(30000, ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[0], ctx->stream);
-    if (e == cudaSuccess) e = launch_plan(p->d_cfg, p->d_state, p->ncl_launch, ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], ctx->stream);
-    if (e == cudaSuccess)
-      e = launch_pair_pass(false, s->dp, ctx->prm.color_mode, p->nblocks, p->d_cfg, p->d_state,
-                           p->d_partials, 0, 0, ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2], ctx->stream);
-    if (e == cudaSuccess)
-      e = launch_pair_pass(true, s->dp, ctx->prm.color_mode, p->nblocks, p->d_cfg, p->d_state,
-                           p->d_partials, 0, 0, ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3], ctx->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) break;
-    if (nrec < max_records) {
-      cvo_iter_profile& r = records[nrec++];
-      r.ell = ells[std::min<size_t>(k, ells.size() - 1)];
-      cudaEventElapsedTime(&r.plan_ms, ev[0], ev[1]);
-      cudaEventElapsedTime(&r.grad_ms, ev[1], ev[2]);
-      cudaEventElapsedTime(&r.step_ms, ev[2], ev[3]);
-      const unsigned long long pass_total = hs->nnz_total - prev_total;
-      r.grad_pairs = (int64_t)hs->nnz_eval;
-      r.step_pairs = (int64_t)(pass_total - hs->nnz_eval);
-      r.grad_candidates = (int64_t)hs->cand_eval;
-      r.step_candidates = 0;
-    }
-    prev_total = hs->nnz_total;
-  }
-  destroy();
-  if (e != cudaSuccess) return fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e));
-  // the step pass visits exactly the candidates of the gradient pass
-  for (int i = 0; i < nrec; ++i) records[i].step_candidates = records[i].grad_candidates;
-  if (n_records) *n_records = nrec;
+  rc = run_solve(ctx, p, P0, true);
+  const SolveState* hs = ctx->h_state;
   std::memcpy(P_out, hs->P, sizeof(double) * 16);
   fill_stats(hs, stats);
-  if (hs->status != 0) return fail(ctx, CVO_ERR_INTERNAL, "cell-row segment overflow");
+  if (stats) stats->status = rc;
+  if (rc != CVO_OK) return rc;
+  const int nrec = std::min(hs->iter, max_records);
+  if (nrec > 0) {
+    std::vector<IterRecord> rec(nrec);
+    CK(cudaMemcpy(rec.data(), p->d_records, sizeof(IterRecord) * nrec, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nrec; ++i) {
+      cvo_iter_profile& r = records[i];
+      r.ell = rec[i].ell;
+      r.plan_ms = rec[i].t_plan_ns * 1e-6f;
+      r.grad_ms = rec[i].t_grad_ns * 1e-6f;
+      r.step_ms = rec[i].t_step_ns * 1e-6f;
+      r.grad_pass_ms = rec[i].t_grad_pass_ns * 1e-6f;
+      r.grad_sync_ms = rec[i].t_grad_sync_ns * 1e-6f;
+      r.step_pass_ms = rec[i].t_step_pass_ns * 1e-6f;
+      r.step_sync_ms = rec[i].t_step_sync_ns * 1e-6f;
+      r.replanned = rec[i].replanned;
+      r.grad_pairs = rec[i].grad_pairs;
+      r.step_pairs = rec[i].step_pairs;
+      r.grad_candidates = rec[i].grad_candidates;
+      r.step_candidates = rec[i].grad_candidates;
+    }
+  }
+  if (n_records) *n_records = nrec;
   return CVO_OK;
 }
 

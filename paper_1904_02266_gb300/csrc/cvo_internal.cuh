@@ -19,14 +19,14 @@ constexpr int kMaxLevels = 8;             // target cell lists one solve may use
 constexpr int kMaxFeatPad = 8;            // padded feature planes (3, 5 or 8)
 constexpr int kMaxPoints = 1 << 22;       // largest cloud (keeps candidate counts in int32)
 constexpr int kMaxCells = 1 << 22;        // largest cell list
-constexpr int kPartialStride = 8;         // doubles per block partial
+constexpr int kPartialStride = 10;        // doubles per block partial
 constexpr int kClusterMax = 32;           // source points per cluster
 constexpr int kMaxSeg = 64;               // cell-row segments per cluster
 constexpr int kMortonBits = 10;           // Morton quantisation per axis
 
 enum : int { kColorNone = 0, kColorKernel = 1, kColorDot = 2 };
 enum : int { kModeAlign = 0, kModeEval = 1 };
-enum : int { kStatusSegOverflow = 1 };    // bit set in SolveState::status
+enum : int { kStatusSegOverflow = 1, kStatusTimeout = 2 };   // bits of SolveState::status
 
 // One uniform-grid cell list over a target cloud (Sec. 5 sparsification:
 // only cells within the cutoff radius of a source point are visited).
@@ -70,15 +70,14 @@ struct SolveCfg {
   SourceView src;
   const IterConst* iters;  // one entry per iteration (one in eval mode)
   // per-iteration work buffers, sized for the largest level
-  float4* zt;              // transformed source points, m_pad
   int* seg_xs;             // first target index of each segment, ncl_max * kMaxSeg
   int* seg_pref;           // candidate offset of each segment in its cluster
   int* cl_nseg;            // segments per cluster
   int* cl_cand;            // candidates per cluster
-  int* chunk_pref;         // ncl_max + 1: exclusive prefix of 32-candidate chunks
-  int* warp_start;         // first cluster of each pair-pass warp
-  int nwarps;              // warps of a pair pass (= nblocks * kWarps)
-  int nblocks;             // blocks of a pair pass
+  long long* group_agg;    // work of each group of 32 consecutive clusters
+  double src_radius;       // max |z'| over the centred source (bounds pose drift)
+  int cost_chunk;          // work model: a chunk costs cs4 + cost_chunk pair tests,
+  int cost_cluster;        //   staging a cluster cost_cluster
   double cX[3], cZ[3];     // FP64 centroids
   double sigma2, a2, b2;
   double ell_floor, eps_pose, eps_grad;
@@ -105,11 +104,17 @@ struct SolveState {
   unsigned long long nnz_total, cand_total;
   unsigned long long nnz_pass[2], cand_pass[2];
   unsigned long long nnz_eval, cand_eval;   // gradient pass of the last iteration
-  unsigned int ticket[2];
-  // FP32 constants of the current iteration (centred frames)
-  float R[9], T[3];          // z~' = R z' + T
-  float om[3], vc[3];        // unit step direction: omega, v + omega x cX
-  float A, rc2, rprune, inv_l2f;
+  unsigned int bar_count, bar_gen;          // grid barrier (zeroed before each launch)
+};
+
+// Per-iteration record of a profiled solve (device timestamps).
+struct IterRecord {
+  double ell;
+  float t_plan_ns, t_grad_ns, t_step_ns;     // %globaltimer intervals on block 0
+  float t_grad_pass_ns, t_grad_sync_ns;      // sub-phases of the gradient interval:
+  float t_step_pass_ns, t_step_sync_ns;      //   block 0's own pass, and pass + barrier
+  int replanned;
+  long long grad_pairs, step_pairs, grad_candidates;
 };
 
 // ---- grid.cu --------------------------------------------------------------
@@ -157,14 +162,12 @@ cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int 
                        float4* out_xyz, float* out_feat, int* cell_start, cudaStream_t s);
 
 // ---- pair_kernels.cu -------------------------------------------------------
-// The kernels of one solve iteration: init (once), then plan, chunk split,
-// gradient pass and step pass. ncl_launch: largest cluster count of any level.
-cudaError_t launch_delay(unsigned ns, cudaStream_t s);
-cudaError_t launch_init(const SolveCfg* cfg, SolveState* st, cudaGraphConditionalHandle cond,
-                        int use_cond, cudaStream_t s);
-cudaError_t launch_plan(const SolveCfg* cfg, SolveState* st, int ncl_launch, cudaStream_t s);
-cudaError_t launch_pair_pass(bool step, int dp, int color_mode, int nblocks,
-                             const SolveCfg* cfg, SolveState* st, double* partials,
-                             cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s);
+// The whole solve (or one evaluation, cfg->mode == kModeEval) as one
+// cooperative launch of nblocks blocks; partials holds 2 * nblocks *
+// kPartialStride doubles; records (may be NULL) one entry per iteration.
+cudaError_t launch_solve(int dp, int color_mode, int nblocks, const SolveCfg* cfg, SolveState* st,
+                         double* partials, IterRecord* records, cudaStream_t s);
+// Co-resident blocks per SM of the solve kernel for this feature layout.
+int solve_blocks_per_sm(int dp, int color_mode);
 
 }  // namespace cvo

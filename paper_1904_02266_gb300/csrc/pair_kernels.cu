@@ -1,5 +1,6 @@
 // The CVO hot path on sm_103a: the cutoff-truncated all-pairs kernel
-// reductions behind one gradient-ascent iteration, plus the FP64 tail.
+// reductions behind each gradient-ascent iteration, plus the FP64 tail, all in
+// one persistent cooperative kernel per solve.
 //
 //  gradient pass  F = sum c_ij k(x_i, z~_j)                         (Eq. scalar)
 //                 dF/domega = (1/ell^2) sum w_ij (z~_j x e_ij)      (Eq. 3_gradient,
@@ -9,21 +10,28 @@
 //                 quartic, P <- exp(t* xi) P (Eqs. newstep, step), lengthscale
 //                 schedule and the Table 1 convergence test.
 //
-// One iteration is four kernels:
-//  plan        one warp per source cluster (an octree node of the source, at
-//              most 32 points): transform the points, take their bounding box
-//              and record the rows of target cells (contiguous runs of the
-//              cell-sorted target) that lie within the cutoff radius of it.
-//  chunk_scan  cut every cluster's candidate list into 32-candidate chunks and
-//              split the chunks evenly over all warps of the pair passes.
-//  pair passes each lane owns one candidate target point (coalesced load into
-//              registers) and loops over the cluster's source points, which the
-//              warp keeps in shared memory and reads as broadcasts. Pair
-//              arithmetic is FP32 with one ex2.approx per kept pair. Per-lane
-//              FP32 sums are reduced in a fixed tree, blocks in FP64 by the
-//              last block to finish, so results are bitwise reproducible.
-// The static, even split keeps every SM busy to the end of the pass however
-// uneven the clusters are.
+// One iteration (every block runs the same sequence; phases are separated by
+// a grid barrier whose spin is bounded):
+//  plan        (only when needed) one warp per source cluster (an octree node
+//              of the source, at most 32 points): transform, bounding box, and
+//              the rows of target cells within the plan radius, stored as
+//              segments of the cell-sorted target.                     barrier
+//              pair-test totals of groups of 32 clusters.               barrier
+//              every block scans the group totals and places its own warps on
+//              an even split of the pair tests (no further barrier).
+//  gradient    each warp walks its share of 32-candidate chunks: one lane per
+//  pass        candidate target point (coalesced load into registers, next
+//              chunk prefetched) against the cluster's source points staged in
+//              shared memory (broadcast reads). FP32 pairs, one ex2.approx per
+//              kept pair, per-lane FP32 sums, fixed-order reductions.  barrier
+//  tail        every block reduces all block partials in FP64 in the same
+//              order and runs the same FP64 tail, so no broadcast is needed.
+//  step pass   as above along the unit direction.                      barrier
+//  tail        step length, exponential-map update, next iteration.
+// The plan is reused while it still covers the cutoff: it is built with a
+// radius 10% wider than the cutoff and rebuilt when the grid level changes,
+// when the pose has drifted by more than that margin (an FP64 bound over the
+// whole source cloud), or when it has become much wider than needed.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,11 +43,26 @@ namespace {
 
 constexpr float kFar = 1.0e18f;   // coordinate of padding points: never within any cutoff
 constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kSpinLimit = 1u << 22;   // barrier polls before giving up (~2 s)
+constexpr double kSkin = 0.10;              // plan radius margin (fraction of the cutoff)
+constexpr double kLoose = 1.25;             // replan when the plan radius exceeds this factor
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ int cell_floor(float v, float o, float inv_h, int n) {
@@ -61,8 +84,25 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 tail
+// per-block iteration state (identical in every block)
 // ---------------------------------------------------------------------------
+
+struct BlockCtx {
+  double P[16];           // current pose
+  double Rp[9], Tp[3];    // centred pose at the last plan
+  double xi[6];
+  double xi_norm, F;
+  double S[5];
+  double t, t_prev;
+  double ell, inv_l2, r_plan, plan_ell;
+  int k, level, plan_level;
+  int need_plan, done, converged, fallback, no_ascent, have_t_prev;
+  unsigned long long nnz_total, cand_total, nnz_grad, cand_grad;
+  float R[9], T[3];       // FP32 centred pose: z~' = R z' + T
+  float om[3], vc[3];     // unit step direction (centred frame)
+  float A, rc2, rplan_f, inv_l2f;
+  int w_c0[kWarps], w_j0[kWarps], w_c1[kWarps], w_j1[kWarps];   // warp ranges
+};
 
 __device__ __forceinline__ void cross3d(const double a[3], const double b[3], double o[3]) {
   o[0] = a[1] * b[2] - a[2] * b[1];
@@ -70,27 +110,61 @@ __device__ __forceinline__ void cross3d(const double a[3], const double b[3], do
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Constants of iteration k (from the host table) and the FP32 pose.
-__device__ void load_iteration(const SolveCfg* cfg, SolveState* st, const IterConst& ic) {
-  st->ell = ic.ell;
-  st->level = ic.level;
-  st->A = ic.A;
-  st->rc2 = ic.rc2;
-  st->rprune = ic.rprune;
-  st->inv_l2f = (float)ic.inv_l2;
-}
-
-__device__ void set_pose_constants(const SolveCfg* cfg, SolveState* st) {
-  const double* P = st->P;
+// Centred pose in FP64: R and T' = R cZ + T - cX.
+__device__ void centred_pose(const SolveCfg* cfg, const double P[16], double R[9], double T[3]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     double tr = P[4 * r + 3] - cfg->cX[r];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      st->R[3 * r + c] = (float)P[4 * r + c];
+      R[3 * r + c] = P[4 * r + c];
       tr = fma(P[4 * r + c], cfg->cZ[c], tr);
     }
-    st->T[r] = (float)tr;
+    T[r] = tr;
+  }
+}
+
+// Iteration k's constants from the host table, the FP32 pose, and whether the
+// traversal plan must be rebuilt.
+__device__ void begin_iteration(const SolveCfg* cfg, BlockCtx& b) {
+  const IterConst ic = cfg->iters[b.k];
+  b.ell = ic.ell;
+  b.inv_l2 = ic.inv_l2;
+  b.A = ic.A;
+  b.rc2 = ic.rc2;
+  b.inv_l2f = (float)ic.inv_l2;
+  double R[9], T[3];
+  centred_pose(cfg, b.P, R, T);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) b.R[i] = (float)R[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) b.T[i] = (float)T[i];
+  // is the current plan still a superset of the pairs within the cutoff?
+  const double need = (double)ic.rprune;   // 1.001 r_c
+  // reuse only at an unchanged lengthscale (the floor of the schedule): while
+  // ell shrinks a fresh, tighter plan costs less than the extra candidates
+  bool replan = b.need_plan || ic.level != b.plan_level || ic.ell != b.plan_ell;
+  if (!replan) {
+    double dr = 0.0, dt = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dr += (R[i] - b.Rp[i]) * (R[i] - b.Rp[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dt += (T[i] - b.Tp[i]) * (T[i] - b.Tp[i]);
+    // |dR z + dT| <= |dR|_F |z| + |dT| for every source point, |z| <= r_src
+    const double drift = sqrt(dr) * cfg->src_radius + sqrt(dt) + 1e-6 * need;
+    replan = (need + drift > b.r_plan) || (b.r_plan > kLoose * (need + drift));
+  }
+  b.level = ic.level;
+  if (replan) {
+    b.need_plan = 1;
+    b.plan_level = ic.level;
+    b.plan_ell = ic.ell;
+    b.r_plan = need * (1.0 + kSkin);
+    b.rplan_f = (float)b.r_plan;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) b.Rp[i] = R[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b.Tp[i] = T[i];
   }
 }
 
@@ -112,8 +186,8 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
         const double q = -0.5 * (c1 + copysign(sqrt(disc), c1));
         const double ra = q / c2, rb = c0 / q;
         const double lo = fmin(ra, rb), hi = fmax(ra, rb);
-        // c2 < 0: + between the roots; crossing + -> - at the larger root.
-        // c2 > 0: crossing + -> - at the smaller root.
+        // c2 < 0: + between the roots, so + -> - at the larger root;
+        // c2 > 0: + outside them, so + -> - at the smaller root
         t = (c2 < 0.0) ? hi : lo;
         if (!(t > 0.0)) t = -1.0;
       }
@@ -202,161 +276,146 @@ __device__ void exp_se3(const double tw[6], double dR[9], double dT[3]) {
     dT[i] = V[3 * i] * rho[0] + V[3 * i + 1] * rho[1] + V[3 * i + 2] * rho[2];
 }
 
-// Gradient-pass finaliser: sums -> F, metric gradient, unit step direction.
-__device__ void finish_gradient(const SolveCfg* cfg, SolveState* st, const double sums[7]) {
-  const double inv_l2 = cfg->iters[cfg->mode == kModeEval ? 0 : st->iter].inv_l2;
+// Gradient tail: sums (F, omega', v, pairs, candidates) -> F, metric
+// gradient, unit step direction in the centred frame.
+__device__ void finish_gradient(const SolveCfg* cfg, BlockCtx& b, const double sums[9]) {
   const double s2 = cfg->sigma2;
   const double v[3] = {sums[4], sums[5], sums[6]};
   double cxv[3];
   cross3d(cfg->cX, v, cxv);
-  const double ka = s2 * inv_l2 / cfg->a2, kb = s2 * inv_l2 / cfg->b2;
-  double xi[6];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    xi[a] = (sums[1 + a] + cxv[a]) * ka;
-    xi[3 + a] = v[a] * kb;
-  }
+  const double ka = s2 * b.inv_l2 / cfg->a2, kb = s2 * b.inv_l2 / cfg->b2;
   double nrm2 = 0.0;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) nrm2 += xi[a] * xi[a];
-  const double nrm = sqrt(nrm2);
+  for (int a = 0; a < 3; ++a) {
+    b.xi[a] = (sums[1 + a] + cxv[a]) * ka;
+    b.xi[3 + a] = v[a] * kb;
+  }
 #pragma unroll
-  for (int a = 0; a < 6; ++a) st->xi[a] = xi[a];
-  st->xi_norm = nrm;
-  st->F = s2 * sums[0];
-  // direction for the step pass in the centred frame: omega, v + omega x cX
+  for (int a = 0; a < 6; ++a) nrm2 += b.xi[a] * b.xi[a];
+  const double nrm = sqrt(nrm2);
+  b.xi_norm = nrm;
+  b.F = s2 * sums[0];
+  b.nnz_grad = (unsigned long long)sums[7];
+  b.cand_grad = (unsigned long long)sums[8];
   double wxc[3];
-  cross3d(xi, cfg->cX, wxc);
+  cross3d(b.xi, cfg->cX, wxc);
   const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    st->om[a] = (float)(xi[a] * inv);
-    st->vc[a] = (float)((xi[3 + a] + wxc[a]) * inv);
+    b.om[a] = (float)(b.xi[a] * inv);
+    b.vc[a] = (float)((b.xi[3 + a] + wxc[a]) * inv);
   }
-  // counters were bumped by other blocks of this kernel: read past L1
-  st->nnz_eval = __ldcg(&st->nnz_pass[0]);
-  st->cand_eval = __ldcg(&st->cand_pass[0]);
 }
 
-// Step-pass finaliser: S0..S4, step length, pose update, schedule, stop test.
-__device__ void finish_step(const SolveCfg* cfg, SolveState* st, const double sums[5],
-                            cudaGraphConditionalHandle cond, int use_cond) {
-  const double nxi = st->xi_norm;
-  double S[5];
+// Step tail: S0..S4, step length, pose update, stop test.
+__device__ void finish_step(const SolveCfg* cfg, BlockCtx& b, const double sums[7]) {
+  const double nxi = b.xi_norm;
   double pw = cfg->sigma2;
 #pragma unroll
   for (int m = 0; m < 5; ++m) {  // the sums were taken along xi / |xi|
-    S[m] = sums[m] * pw;
+    b.S[m] = sums[m] * pw;
     pw *= nxi;
   }
-#pragma unroll
-  for (int m = 0; m < 5; ++m) st->S[m] = S[m];
-  st->nnz_total += __ldcg(&st->nnz_pass[0]) + __ldcg(&st->nnz_pass[1]);
-  st->cand_total += __ldcg(&st->cand_pass[0]) + __ldcg(&st->cand_pass[1]);
+  b.nnz_total += b.nnz_grad + (unsigned long long)sums[5];
+  b.cand_total += b.cand_grad + (unsigned long long)sums[6];
   if (cfg->mode == kModeEval) {
-    st->done = 1;
-    if (use_cond) cudaGraphSetConditional(cond, 0u);
+    b.done = 1;
     return;
   }
   double t;
-  if (!(nxi > 0.0) || !(S[1] > 0.0)) {
+  if (!(nxi > 0.0) || !(b.S[1] > 0.0)) {
     t = 0.0;
-    st->no_ascent_steps += 1;
+    b.no_ascent += 1;
   } else {
     bool ok;
     if (cfg->step_order == 2) {
-      ok = S[2] < 0.0;
-      t = ok ? -S[1] / (2.0 * S[2]) : 0.0;
+      ok = b.S[2] < 0.0;
+      t = ok ? -b.S[1] / (2.0 * b.S[2]) : 0.0;
     } else {
-      ok = first_maximiser(S[1], 2.0 * S[2], 3.0 * S[3], 4.0 * S[4], &t);
+      ok = first_maximiser(b.S[1], 2.0 * b.S[2], 3.0 * b.S[3], 4.0 * b.S[4], &t);
     }
     if (!ok) {
-      st->fallback_steps += 1;
-      t = st->have_t_prev ? 0.5 * st->t_prev : 1e-3 / nxi;
+      b.fallback += 1;
+      t = b.have_t_prev ? 0.5 * b.t_prev : 1e-3 / nxi;
     }
   }
   // P <- exp(t xi) P
   double tw[6], dR[9], dT[3];
 #pragma unroll
-  for (int a = 0; a < 6; ++a) tw[a] = t * st->xi[a];
+  for (int a = 0; a < 6; ++a) tw[a] = t * b.xi[a];
   exp_se3(tw, dR, dT);
-  double Pn[16];
+  double Pn[12];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      Pn[4 * r + c] = dR[3 * r] * st->P[c] + dR[3 * r + 1] * st->P[4 + c] + dR[3 * r + 2] * st->P[8 + c];
+      Pn[4 * r + c] = dR[3 * r] * b.P[c] + dR[3 * r + 1] * b.P[4 + c] + dR[3 * r + 2] * b.P[8 + c];
     Pn[4 * r + 3] += dT[r];
   }
 #pragma unroll
-  for (int i = 0; i < 12; ++i) st->P[i] = Pn[i];
-  st->t = t;
-  st->t_prev = t;
-  st->have_t_prev = 1;
-  const int k = st->iter;
-  st->iter = k + 1;
-  const bool conv = (st->ell == cfg->ell_floor) &&
+  for (int i = 0; i < 12; ++i) b.P[i] = Pn[i];
+  b.t = t;
+  b.t_prev = t;
+  b.have_t_prev = 1;
+  const bool conv = (b.ell == cfg->ell_floor) &&
                     (fabs(t) * nxi < cfg->eps_pose || nxi < cfg->eps_grad);
-  if (conv || st->iter >= cfg->max_iters) {
-    st->done = 1;
-    st->converged = conv ? 1 : 0;
-  } else {
-    load_iteration(cfg, st, cfg->iters[st->iter]);
-    set_pose_constants(cfg, st);
+  b.k += 1;
+  if (conv || b.k >= cfg->max_iters) {
+    b.done = 1;
+    b.converged = conv ? 1 : 0;
   }
-  if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
 }
 
-// ---------------------------------------------------------------------------
-// kernels
-// ---------------------------------------------------------------------------
-
-__global__ void init_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
-                            cudaGraphConditionalHandle cond, int use_cond) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = 0; i < 16; ++i) st->P[i] = st->P0[i];
-  st->iter = 0;
-  st->done = 0;
-  st->converged = 0;
-  st->fallback_steps = 0;
-  st->no_ascent_steps = 0;
-  st->have_t_prev = 0;
-  st->status = 0;
-  st->t = 0.0;
-  st->t_prev = 0.0;
-  st->nnz_total = 0;
-  st->cand_total = 0;
-  st->nnz_pass[0] = st->nnz_pass[1] = 0;
-  st->cand_pass[0] = st->cand_pass[1] = 0;
-  st->nnz_eval = st->cand_eval = 0;
-  st->ticket[0] = st->ticket[1] = 0;
-  if (cfg->max_iters <= 0) st->done = 1;
-  load_iteration(cfg, st, cfg->iters[0]);
-  set_pose_constants(cfg, st);
-  if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+// Bounded grid barrier. Every block calls it the same number of times; the
+// cooperative launch keeps all blocks resident. A block that polls for
+// kSpinLimit rounds raises kStatusTimeout and every block then leaves the
+// solve loop at its next barrier.
+__device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicExch(&st->bar_gen, g + 1);
+    } else {
+      unsigned spins = 0;
+      while (ld_acquire(&st->bar_gen) == g) {
+        if (++spins > kSpinLimit) {
+          ok = 0;
+          atomicOr(&st->status, (int)kStatusTimeout);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    gen = g + 1;
+    if (ld_acquire((const unsigned*)&st->status) & kStatusTimeout) ok = 0;
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
 }
 
-// One warp per source cluster: transform its points, and list the target
-// cell rows within the cutoff of its bounding box as (first index, offset)
-// segments of the cell-sorted target.
-__global__ void __launch_bounds__(kThreads)
-plan_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int level = st->level;
-  const ClusterView cv = cfg->clusters[level];
-  if (c >= cv.ncl) return;
-  const GridView g = cfg->grids[level];
+// Plan of one cluster (one warp): transform its points, bounding box, cell
+// rows within the plan radius -> segments, candidate count.
+__device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState* st, int c,
+                             int lane) {
+  const GridView& g = cfg->grids[b.level];
+  const ClusterView& cv = cfg->clusters[b.level];
   const int p0 = cv.cstart[c];
   const int cs = cv.cstart[c + 1] - p0;
   const bool zv = lane < cs;
   float zx = 0.f, zy = 0.f, zz = 0.f;
   if (zv) {
     const float4 p = cfg->src.xyz[p0 + lane];
-    zx = fmaf(st->R[0], p.x, fmaf(st->R[1], p.y, fmaf(st->R[2], p.z, st->T[0])));
-    zy = fmaf(st->R[3], p.x, fmaf(st->R[4], p.y, fmaf(st->R[5], p.z, st->T[1])));
-    zz = fmaf(st->R[6], p.x, fmaf(st->R[7], p.y, fmaf(st->R[8], p.z, st->T[2])));
-    cfg->zt[p0 + lane] = make_float4(zx, zy, zz, 0.f);
+    zx = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
+    zy = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
+    zz = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
   }
   float blo[3] = {zv ? zx : INFINITY, zv ? zy : INFINITY, zv ? zz : INFINITY};
   float bhi[3] = {zv ? zx : -INFINITY, zv ? zy : -INFINITY, zv ? zz : -INFINITY};
@@ -368,7 +427,7 @@ plan_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st) {
       bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(kFull, bhi[a], off));
     }
   }
-  const float rp = st->rprune;
+  const float rp = b.rplan_f;
   const float rp2 = rp * rp;
   const int cx0 = max(0, cell_floor(blo[0] - rp, g.ox, g.inv_h, g.nx));
   const int cx1 = min(g.nx - 1, cell_floor(bhi[0] + rp, g.ox, g.inv_h, g.nx));
@@ -421,114 +480,180 @@ plan_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st) {
     nseg += __popc(m);
     total += __shfl_sync(kFull, incl, 31);
   }
-  if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&st->status, kStatusSegOverflow);
+  if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&st->status, (int)kStatusSegOverflow);
   if (lane == 0) {
     cfg->cl_nseg[c] = min(nseg, kMaxSeg);
     cfg->cl_cand[c] = total;
   }
 }
 
-// Exclusive prefix of 32-candidate chunks over the clusters, and the first
-// cluster of every pair-pass warp (warp w owns chunks
-// [floor(w TC / NW), floor((w + 1) TC / NW))).
-__global__ void __launch_bounds__(1024)
-chunk_scan_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st) {
-  __shared__ int s_sum[1024];
-  const int tid = threadIdx.x;
-  const int ncl = cfg->clusters[st->level].ncl;
-  const int per = (ncl + 1023) / 1024;
-  const int b = min(ncl, tid * per), e = min(ncl, b + per);
-  int local = 0;
-  for (int c = b; c < e; ++c) local += (__ldcg(&cfg->cl_cand[c]) + 31) >> 5;
-  s_sum[tid] = local;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const int v = tid >= off ? s_sum[tid - off] : 0;
-    __syncthreads();
-    s_sum[tid] += v;
-    __syncthreads();
-  }
-  const long long TC = s_sum[1023];
-  const long long NW = cfg->nwarps;
-  int run = s_sum[tid] - local;
-  for (int c = b; c < e; ++c) {
-    const int ch = (__ldcg(&cfg->cl_cand[c]) + 31) >> 5;
-    cfg->chunk_pref[c] = run;
-    if (ch > 0) {
-      const long long g0 = ((long long)run * NW + TC - 1) / TC;
-      const long long g1 = ((long long)(run + ch) * NW + TC - 1) / TC;
-      for (long long w = g0; w < g1; ++w) cfg->warp_start[w] = c;
-    }
-    run += ch;
-  }
-  if (tid == 1023) cfg->chunk_pref[ncl] = (int)TC;
+// Work of cluster c under the current plan, in pair-test units: staging the
+// cluster costs cost_cluster, each 32-candidate chunk its cs4 pair tests per
+// lane (cluster size padded to a multiple of 4) plus cost_chunk of per-chunk
+// overhead. Chunk j starts at offset cost_cluster + j * (cs4 + cost_chunk).
+__device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const ClusterView& cv,
+                                                  int c, int* k_out) {
+  const int tc = __ldcg(&cfg->cl_cand[c]);
+  const int cs4 = ((cv.cstart[c + 1] - cv.cstart[c]) + 3) & ~3;
+  const int k = cs4 + cfg->cost_chunk;
+  *k_out = k;
+  const int nch = (tc + 31) >> 5;
+  return nch > 0 ? (long long)cfg->cost_cluster + (long long)nch * k : 0;
 }
 
-template <bool STEP, int DP, int MODE>
-__global__ void __launch_bounds__(kThreads)
-pair_pass_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
-                 double* __restrict__ partials, cudaGraphConditionalHandle cond, int use_cond) {
-  constexpr int NACC = STEP ? 5 : 7;
-  constexpr int DPS = DP > 0 ? DP : 1;
-  constexpr int NU = STEP ? 4 : 1;
-  __shared__ float4 s_z[kWarps][kClusterMax];
-  __shared__ float s_zf[kWarps][DPS][kClusterMax];
-  __shared__ float4 s_u[kWarps][NU][kClusterMax];
-  __shared__ int s_xs[kWarps][kMaxSeg];
-  __shared__ int s_pf[kWarps][kMaxSeg + 1];
-  __shared__ float s_red[kWarps][NACC];
-  __shared__ double s_fin[kWarps][NACC];
-  __shared__ int s_last;
+// Shared memory of the solve kernel.
+template <int DPS, int NU>
+struct SolveSmem {
+  float4 z[kWarps][kClusterMax];
+  float zf[kWarps][DPS][kClusterMax];
+  float4 u[kWarps][NU][kClusterMax];
+  int xs[kWarps][kMaxSeg];
+  int pf[kWarps][kMaxSeg + 1];
+  float red[kWarps][10];
+  long long scan[kThreads];
+  long long bnd_base[2 * kWarps];   // work offset of the group holding each warp boundary
+  int bnd_group[2 * kWarps];
+  double sums[10];
+  int flag;
+  BlockCtx b;
+};
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const long long gw = (long long)blockIdx.x * kWarps + warp;
-  const int level = st->level;
-  const GridView g = cfg->grids[level];
-  const ClusterView cv = cfg->clusters[level];
-  const float rc2 = st->rc2, A = st->A;
-  float om[3] = {0.f, 0.f, 0.f}, vc[3] = {0.f, 0.f, 0.f};
-  float inv_l2 = 0.f;
-  if (STEP) {
+// (cluster, chunk) of the first chunk whose work starts at or after s, for s
+// inside group `group` whose work starts at `base` (one warp). The chunk may
+// equal the cluster's chunk count, which means the next cluster's first chunk.
+__device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, long long base,
+                       long long s, int lane, int* c_out, int* j_out) {
+  const int c = group * 32 + lane;
+  long long w = 0;
+  int kk = 4;
+  if (c < cv.ncl) w = cluster_work(cfg, cv, c, &kk);
+  long long incl = w;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      om[i] = st->om[i];
-      vc[i] = st->vc[i];
-    }
-    inv_l2 = st->inv_l2f;
+  for (int off = 1; off < 32; off <<= 1) {
+    const long long v = __shfl_up_sync(kFull, incl, off);
+    if (lane >= off) incl += v;
   }
+  const long long excl = base + incl - w;
+  const unsigned m = __ballot_sync(kFull, c < cv.ncl && w > 0 && s >= excl && s < excl + w);
+  if (m) {
+    const int src = __ffs(m) - 1;
+    const long long e = __shfl_sync(kFull, excl, src) + cfg->cost_cluster;
+    const int k4 = __shfl_sync(kFull, kk, src);
+    *c_out = group * 32 + src;
+    *j_out = s <= e ? 0 : (int)((s - e + k4 - 1) / k4);
+  } else {
+    *c_out = min(group * 32 + 32, cv.ncl);
+    *j_out = 0;
+  }
+}
 
-  float acc[NACC];
+// Place the block's warps on an even split of the plan's work: warp w owns the
+// chunks whose work starts in [floor(w TW/NW), floor((w+1) TW/NW)).
+template <int DPS, int NU>
+__device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid) {
+  const ClusterView& cv = cfg->clusters[sm.b.level];
+  const int ng = (cv.ncl + 31) / 32;
+  const int per = (ng + kThreads - 1) / kThreads;
+  const int g0 = min(ng, tid * per), g1 = min(ng, g0 + per);
+  long long local = 0;
+  for (int gi = g0; gi < g1; ++gi) local += __ldcg(&cfg->group_agg[gi]);
+  sm.scan[tid] = local;
+  if (tid < 2 * kWarps) sm.bnd_group[tid] = -1;
+  __syncthreads();
+  for (int off = 1; off < kThreads; off <<= 1) {
+    const long long v = tid >= off ? sm.scan[tid - off] : 0;
+    __syncthreads();
+    sm.scan[tid] += v;
+    __syncthreads();
+  }
+  const long long TW = sm.scan[kThreads - 1];
+  const long long NW = (long long)gridDim.x * kWarps;
+  long long run = sm.scan[tid] - local;
+  for (int gi = g0; gi < g1; ++gi) {
+    const long long gtests = __ldcg(&cfg->group_agg[gi]);
 #pragma unroll
-  for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
-  unsigned int nnz = 0, cand = 0;
-
-  const long long TC = __ldcg(&cfg->chunk_pref[cv.ncl]);
-  const long long NW = cfg->nwarps;
-  const int ch0 = (int)((gw * TC) / NW), ch1 = (int)(((gw + 1) * TC) / NW);
-  int c = 0, loaded = -1, cs4 = 0, tc = 0, nseg = 0, cpref = 0, cnext = 0;
-  if (ch0 < ch1) {
-    c = __ldcg(&cfg->warp_start[gw]);
-    cpref = __ldcg(&cfg->chunk_pref[c]);
-    cnext = __ldcg(&cfg->chunk_pref[c + 1]);
-  }
-  for (int ch = ch0; ch < ch1; ++ch) {
-    while (ch >= cnext) {
-      ++c;
-      cpref = cnext;
-      cnext = __ldcg(&cfg->chunk_pref[c + 1]);
+    for (int q = 0; q < 2 * kWarps; ++q) {
+      const long long w = (long long)blockIdx.x * kWarps + (q >> 1) + (q & 1);
+      const long long s = TW > 0 ? (w * TW) / NW : 0;
+      if (gtests > 0 && s >= run && s < run + gtests) {
+        sm.bnd_group[q] = gi;
+        sm.bnd_base[q] = run;
+      }
     }
+    run += gtests;
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = 2 * warp + h;
+    const long long w = (long long)blockIdx.x * kWarps + warp + h;
+    const long long s = TW > 0 ? (w * TW) / NW : 0;
+    int c, jj;
+    if (TW == 0 || s >= TW || sm.bnd_group[q] < 0) {
+      c = cv.ncl;   // past the end: no chunk
+      jj = 0;
+    } else {
+      locate(cfg, cv, sm.bnd_group[q], sm.bnd_base[q], s, lane, &c, &jj);
+    }
+    if (lane == 0) {
+      if (h == 0) {
+        sm.b.w_c0[warp] = c;
+        sm.b.w_j0[warp] = jj;
+      } else {
+        sm.b.w_c1[warp] = c;
+        sm.b.w_j1[warp] = jj;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// One warp's share of a pair pass; lane sums in acc, counts in nnz / cand.
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
+                          float acc[7], unsigned& nnz, unsigned& cand) {
+  const BlockCtx& b = sm.b;
+  const GridView& g = cfg->grids[b.level];
+  const ClusterView& cv = cfg->clusters[b.level];
+  const float rc2 = b.rc2, A = b.A;
+  int c = b.w_c0[warp], jc = b.w_j0[warp];
+  const int c_end = b.w_c1[warp], j_end = b.w_j1[warp];
+  int loaded = -1, cs = 0, cs4 = 0, tc = 0, nch_c = 0, nseg = 0, seg = 0;
+  float4 xp_next = make_float4(-kFar, -kFar, -kFar, 0.f);
+  float xf_next[DPS];
+#pragma unroll
+  for (int d = 0; d < DPS; ++d) xf_next[d] = 0.f;
+  bool have_next = false;
+  for (;;) {
     if (c != loaded) {
-      // stage cluster c: its transformed points, features, step vectors, segments
-      __syncwarp();   // every lane is done with the previous cluster
+      for (;;) {  // the next cluster that still has a chunk in this warp's range
+        if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) return;
+        tc = __ldcg(&cfg->cl_cand[c]);
+        nch_c = (tc + 31) >> 5;
+        if (jc < nch_c) break;
+        ++c;
+        jc = 0;
+      }
+      __syncwarp();   // every lane is done with the previous cluster's staging
       const int p0 = cv.cstart[c];
-      const int cs = cv.cstart[c + 1] - p0;
+      cs = cv.cstart[c + 1] - p0;
       const bool zv = lane < cs;
       float4 z = make_float4(kFar, kFar, kFar, 0.f);
-      if (zv) z = __ldcg(&cfg->zt[p0 + lane]);
-      s_z[warp][lane] = z;
+      if (zv) {
+        const float4 p = cfg->src.xyz[p0 + lane];
+        z.x = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
+        z.y = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
+        z.z = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
+      }
+      sm.z[warp][lane] = z;
 #pragma unroll
-      for (int d = 0; d < DP; ++d) s_zf[warp][d][lane] = zv ? cfg->src.feat[d * cfg->src.m_pad + p0 + lane] : 0.f;
+      for (int d = 0; d < DP; ++d)
+        sm.zf[warp][d][lane] = zv ? cfg->src.feat[d * cfg->src.m_pad + p0 + lane] : 0.f;
       if (STEP) {
+        const float* om = b.om;
+        const float* vc = b.vc;
+        const float inv_l2 = b.inv_l2f;
         const float zt[3] = {zv ? z.x : 0.f, zv ? z.y : 0.f, zv ? z.z : 0.f};
         float u1[3], u2[3], u3[3], u4[3];
         u1[0] = om[1] * zt[2] - om[2] * zt[1] + vc[0];
@@ -550,48 +675,77 @@ pair_pass_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
         // beta = e.U1; gamma = e.U2 - k2; delta = e.U3 - k3; eps = e.U4 - k4
         const float c1 = inv_l2, c2 = 0.5f * inv_l2, c3 = inv_l2 * (1.0f / 6.0f),
                     c4 = inv_l2 * (1.0f / 24.0f);
-        s_u[warp][0][lane] = make_float4(u1[0] * c1, u1[1] * c1, u1[2] * c1, 0.5f * u11 * inv_l2);
-        s_u[warp][1 % NU][lane] = make_float4(u2[0] * c2, u2[1] * c2, u2[2] * c2, 0.5f * u12 * inv_l2);
-        s_u[warp][2 % NU][lane] = make_float4(u3[0] * c3, u3[1] * c3, u3[2] * c3,
-                                              (u13 * (1.0f / 6.0f) + u22 * 0.125f) * inv_l2);
-        s_u[warp][3 % NU][lane] = make_float4(u4[0] * c4, u4[1] * c4, u4[2] * c4, 0.f);
+        sm.u[warp][0][lane] = make_float4(u1[0] * c1, u1[1] * c1, u1[2] * c1, 0.5f * u11 * inv_l2);
+        sm.u[warp][1 % NU][lane] = make_float4(u2[0] * c2, u2[1] * c2, u2[2] * c2, 0.5f * u12 * inv_l2);
+        sm.u[warp][2 % NU][lane] = make_float4(u3[0] * c3, u3[1] * c3, u3[2] * c3,
+                                               (u13 * (1.0f / 6.0f) + u22 * 0.125f) * inv_l2);
+        sm.u[warp][3 % NU][lane] = make_float4(u4[0] * c4, u4[1] * c4, u4[2] * c4, 0.f);
       }
       nseg = __ldcg(&cfg->cl_nseg[c]);
-      tc = __ldcg(&cfg->cl_cand[c]);
       for (int i = lane; i < nseg; i += 32) {
-        s_xs[warp][i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
-        s_pf[warp][i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
+        sm.xs[warp][i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
+        sm.pf[warp][i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
       }
-      if (lane == 0) s_pf[warp][nseg] = tc;
+      if (lane == 0) sm.pf[warp][nseg] = tc;
       cs4 = (cs + 3) & ~3;
       loaded = c;
+      have_next = false;
       __syncwarp();
-    }
-    // this lane's candidate
-    const int q = (ch - cpref) * 32 + lane;
-    float4 xp = make_float4(-kFar, -kFar, -kFar, 0.f);
-    float xf[DPS];
-#pragma unroll
-    for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
-    if (q < tc) {
-      int lo = 0, hi = nseg;  // s_pf[lo] <= q < s_pf[hi]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_pf[warp][mid] <= q) lo = mid;
-        else hi = mid;
+      // this lane's segment for chunk jc (binary search once per cluster)
+      const int q0 = jc * 32 + lane;
+      int lo = 0, hi = nseg;
+      if (q0 < tc) {
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (sm.pf[warp][mid] <= q0) lo = mid;
+          else hi = mid;
+        }
       }
-      const int xi = s_xs[warp][lo] + (q - s_pf[warp][lo]);
-      xp = g.xyz[xi];
+      seg = lo;
+    }
+    // candidate of chunk jc (prefetched during the previous chunk of the same
+    // cluster) and the prefetch of chunk jc + 1
+    float4 xp;
+    float xf[DPS];
+    if (have_next) {
+      xp = xp_next;
 #pragma unroll
-      for (int d = 0; d < DP; ++d) xf[d] = g.feat[d * g.n_pad + xi];
-      cand += (unsigned)(cv.cstart[c + 1] - cv.cstart[c]);
+      for (int d = 0; d < DPS; ++d) xf[d] = xf_next[d];
+    } else {
+      xp = make_float4(-kFar, -kFar, -kFar, 0.f);
+#pragma unroll
+      for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
+      const int q = jc * 32 + lane;
+      if (q < tc) {
+        while (sm.pf[warp][seg + 1] <= q) ++seg;
+        const int xi = sm.xs[warp][seg] + (q - sm.pf[warp][seg]);
+        xp = g.xyz[xi];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) xf[d] = g.feat[d * g.n_pad + xi];
+      }
+    }
+    if (jc * 32 + lane < tc) cand += (unsigned)cs;
+    const bool last_of_range = (c == c_end && jc + 1 >= j_end);
+    have_next = (jc + 1 < nch_c) && !last_of_range;
+    if (have_next) {
+      xp_next = make_float4(-kFar, -kFar, -kFar, 0.f);
+#pragma unroll
+      for (int d = 0; d < DPS; ++d) xf_next[d] = 0.f;
+      const int q = (jc + 1) * 32 + lane;
+      if (q < tc) {
+        while (sm.pf[warp][seg + 1] <= q) ++seg;
+        const int xi = sm.xs[warp][seg] + (q - sm.pf[warp][seg]);
+        xp_next = g.xyz[xi];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) xf_next[d] = g.feat[d * g.n_pad + xi];
+      }
     }
     float W = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
     for (int j0 = 0; j0 < cs4; j0 += 4) {
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
         const int j = j0 + jj;
-        const float4 z = s_z[warp][j];
+        const float4 z = sm.z[warp][j];
         const float ex = xp.x - z.x, ey = xp.y - z.y, ez = xp.z - z.z;
         const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
         if (d2 <= rc2) {
@@ -600,14 +754,14 @@ pair_pass_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
             float qf = 0.f;
 #pragma unroll
             for (int d = 0; d < DP; ++d) {
-              const float df = xf[d] - s_zf[warp][d][j];
+              const float df = xf[d] - sm.zf[warp][d][j];
               qf = fmaf(df, df, qf);
             }
             w = ex2_approx(-fmaf(A, d2, qf));
           } else if (MODE == kColorDot) {
             float cdot = 0.f;
 #pragma unroll
-            for (int d = 0; d < DP; ++d) cdot = fmaf(xf[d], s_zf[warp][d][j], cdot);
+            for (int d = 0; d < DP; ++d) cdot = fmaf(xf[d], sm.zf[warp][d][j], cdot);
             w = ex2_approx(-A * d2) * cdot;
           } else {
             w = ex2_approx(-A * d2);
@@ -619,8 +773,8 @@ pair_pass_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
             Ey = fmaf(w, ey, Ey);
             Ez = fmaf(w, ez, Ez);
           } else {
-            const float4 U1 = s_u[warp][0][j], U2 = s_u[warp][1 % NU][j];
-            const float4 U3 = s_u[warp][2 % NU][j], U4 = s_u[warp][3 % NU][j];
+            const float4 U1 = sm.u[warp][0][j], U2 = sm.u[warp][1 % NU][j];
+            const float4 U3 = sm.u[warp][2 % NU][j], U4 = sm.u[warp][3 % NU][j];
             const float beta = fmaf(ex, U1.x, fmaf(ey, U1.y, ez * U1.z));
             const float gam = fmaf(ex, U2.x, fmaf(ey, U2.y, fmaf(ez, U2.z, -U1.w)));
             const float del = fmaf(ex, U3.x, fmaf(ey, U3.y, fmaf(ez, U3.z, -U2.w)));
@@ -649,130 +803,246 @@ pair_pass_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
       acc[5] += Ey;
       acc[6] += Ez;
     }
+    if (last_of_range) return;
+    if (++jc >= nch_c) {
+      ++c;
+      jc = 0;
+    }
   }
+}
 
-  // ---- block reduction in a fixed order ----
+// One pass over the block's warps, then the block partial (fixed order).
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials) {
+  constexpr int NACC = STEP ? 5 : 7;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float acc[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) acc[i] = 0.f;
+  unsigned nnz = 0, cand = 0;
+  pass_warp<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, acc, nnz, cand);
+  __syncwarp();
 #pragma unroll
   for (int i = 0; i < NACC; ++i) {
     const float v = warp_sum_f(acc[i]);
-    if (lane == 0) s_red[warp][i] = v;
+    if (lane == 0) sm.red[warp][i] = v;
   }
-  unsigned long long wn = nnz, wc = cand;
+  unsigned wn = nnz, wc = cand;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     wn += __shfl_down_sync(kFull, wn, off);
     wc += __shfl_down_sync(kFull, wc, off);
   }
-  if (lane == 0 && (wn | wc)) {
-    atomicAdd(&st->nnz_pass[STEP ? 1 : 0], wn);
-    atomicAdd(&st->cand_pass[STEP ? 1 : 0], wc);
+  if (lane == 0) {
+    sm.red[warp][NACC] = __uint_as_float(wn);
+    sm.red[warp][NACC + 1] = __uint_as_float(wc);
   }
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 0 && lane < NACC + 2) {
+    double s = 0.0;
     if (lane < NACC) {
-      double s = 0.0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += (double)s_red[w][lane];
-      partials[(size_t)blockIdx.x * kPartialStride + lane] = s;
-      __threadfence();
+      for (int w = 0; w < kWarps; ++w) s += (double)sm.red[w][lane];
+    } else {
+      unsigned long long n = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) n += __float_as_uint(sm.red[w][lane]);
+      s = (double)n;
     }
-    __syncwarp();
-    if (lane == 0) {
-      const unsigned t = atomicAdd(&st->ticket[STEP ? 1 : 0], 1u);
-      s_last = (t == gridDim.x - 1) ? 1 : 0;
-    }
+    partials[(size_t)blockIdx.x * kPartialStride + lane] = s;
   }
-  __syncthreads();
-  if (!s_last) return;
+}
 
-  // ---- last block: fixed-order FP64 reduction of all block partials ----
-  __threadfence();
-  double fin[NACC];
+// Fixed-order FP64 sum of all block partials. Warp w sums values w and w + 8:
+// lane l adds blocks l, l + 32, ... (all loads issued first, then a pairwise
+// tree), then a shuffle tree across lanes. Results land in out[] (shared).
+// Must be called by every thread of the block.
+__device__ void reduce_partials(const double* partials, int nvals, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kMaxPerLane = 16;   // blocks per lane: up to 512 blocks
+  for (int i = warp; i < nvals; i += kWarps) {
+    double v[kMaxPerLane];
 #pragma unroll
-  for (int i = 0; i < NACC; ++i) fin[i] = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += kThreads) {
+    for (int q = 0; q < kMaxPerLane; ++q) {
+      const int b = lane + 32 * q;
+      v[q] = b < (int)gridDim.x ? __ldcg(&partials[(size_t)b * kPartialStride + i]) : 0.0;
+    }
 #pragma unroll
-    for (int i = 0; i < NACC; ++i) fin[i] += __ldcg(&partials[(size_t)b * kPartialStride + i]);
-  }
+    for (int w = kMaxPerLane / 2; w > 0; w >>= 1)
 #pragma unroll
-  for (int i = 0; i < NACC; ++i) {
-    const double v = warp_sum_d(fin[i]);
-    if (lane == 0) s_fin[warp][i] = v;
+      for (int q = 0; q < w; ++q) v[q] += v[q + w];
+    const double s = warp_sum_d(v[0]);
+    if (lane == 0) out[i] = s;
   }
   __syncthreads();
-  if (warp == 0) {
-    if (lane < NACC) {
-      double s = 0.0;
+}
+
+__device__ void publish(SolveState* st, const BlockCtx& b) {
+  for (int i = 0; i < 16; ++i) st->P[i] = b.P[i];
+  for (int i = 0; i < 6; ++i) st->xi[i] = b.xi[i];
+  for (int i = 0; i < 5; ++i) st->S[i] = b.S[i];
+  st->xi_norm = b.xi_norm;
+  st->F = b.F;
+  st->t = b.t;
+  st->ell = b.ell;
+  st->level = b.level;
+  st->iter = b.k;
+  st->done = b.done;
+  st->converged = b.converged;
+  st->fallback_steps = b.fallback;
+  st->no_ascent_steps = b.no_ascent;
+  st->nnz_total = b.nnz_total;
+  st->cand_total = b.cand_total;
+  st->nnz_eval = b.nnz_grad;
+  st->cand_eval = b.cand_grad;
+}
+
+// The whole solve (or one evaluation) in one cooperative launch.
+template <int DP, int MODE>
+__global__ void __launch_bounds__(kThreads)
+solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
+             double* __restrict__ partials, IterRecord* __restrict__ records) {
+  constexpr int DPS = DP > 0 ? DP : 1;
+  constexpr int NU = 4;
+  __shared__ SolveSmem<DPS, NU> sm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned gen = 0;
+  double* part_g = partials;
+  double* part_s = partials + (size_t)gridDim.x * kPartialStride;
+  const long long NW = (long long)gridDim.x * kWarps;
+  const long long gw = (long long)blockIdx.x * kWarps + warp;
+
+  if (tid == 0) {
+    BlockCtx& b = sm.b;
+    for (int i = 0; i < 16; ++i) b.P[i] = st->P0[i];
+    b.k = 0;
+    b.level = 0;
+    b.plan_level = -1;
+    b.need_plan = 1;
+    b.done = cfg->max_iters <= 0 ? 1 : 0;
+    b.converged = b.fallback = b.no_ascent = b.have_t_prev = 0;
+    b.t = b.t_prev = 0.0;
+    b.nnz_total = b.cand_total = b.nnz_grad = b.cand_grad = 0;
+    b.F = b.xi_norm = 0.0;
+    for (int i = 0; i < 6; ++i) b.xi[i] = 0.0;
+    for (int i = 0; i < 5; ++i) b.S[i] = 0.0;
+    b.r_plan = 0.0;
+    b.plan_ell = 0.0;
+    if (!b.done) begin_iteration(cfg, b);
+  }
+  __syncthreads();
+
+  while (!sm.b.done) {
+    unsigned long long t0 = 0, t1 = 0, t2 = 0, tg1 = 0, tg2 = 0, ts1 = 0, ts2 = 0;
+    const bool stamp = records != nullptr && blockIdx.x == 0 && tid == 0;
+    if (stamp) t0 = globaltimer();
+    const int replan = sm.b.need_plan;
+    if (replan) {
+      const ClusterView& cv = cfg->clusters[sm.b.level];
+      for (long long c = gw; c < cv.ncl; c += NW) plan_cluster(cfg, sm.b, st, (int)c, lane);
+      if (!grid_sync(st, gen, &sm.flag)) break;
+      const int ng = (cv.ncl + 31) / 32;
+      for (long long gi = gw; gi < ng; gi += NW) {
+        const int c = (int)gi * 32 + lane;
+        int kk;
+        long long w = c < cv.ncl ? cluster_work(cfg, cv, c, &kk) : 0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += s_fin[w][lane];
-      s_fin[0][lane] = s;
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(kFull, w, off);
+        if (lane == 0) cfg->group_agg[gi] = w;
+      }
+      if (!grid_sync(st, gen, &sm.flag)) break;
+      split_work<DPS, NU>(cfg, sm, tid);
+      if (tid == 0) sm.b.need_plan = 0;
+      __syncthreads();
     }
-    __syncwarp();
-    if (lane == 0) {
-      double sums[NACC];
-#pragma unroll
-      for (int i = 0; i < NACC; ++i) sums[i] = s_fin[0][i];
-      st->ticket[STEP ? 1 : 0] = 0;
-      if (!STEP) {
-        finish_gradient(cfg, st, sums);
-      } else {
-        finish_step(cfg, st, sums, cond, use_cond);
-        st->nnz_pass[0] = st->nnz_pass[1] = 0;
-        st->cand_pass[0] = st->cand_pass[1] = 0;
+    if (stamp) t1 = globaltimer();
+    // ---- gradient pass ----
+    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g);
+    if (stamp) tg1 = globaltimer();
+    if (!grid_sync(st, gen, &sm.flag)) break;
+    if (stamp) tg2 = globaltimer();
+    reduce_partials(part_g, 9, sm.sums);
+    if (tid == 0) finish_gradient(cfg, sm.b, sm.sums);
+    __syncthreads();
+    if (stamp) t2 = globaltimer();
+    // ---- step pass ----
+    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s);
+    if (stamp) ts1 = globaltimer();
+    if (!grid_sync(st, gen, &sm.flag)) break;
+    if (stamp) ts2 = globaltimer();
+    reduce_partials(part_s, 7, sm.sums);
+    {
+      if (tid == 0) {
+        BlockCtx& b = sm.b;
+        const int k = b.k;
+        const unsigned long long pairs_before = b.nnz_total;
+        finish_step(cfg, b, sm.sums);
+        if (stamp && k < cfg->max_iters) {
+          IterRecord& r = records[k];
+          r.ell = b.ell;
+          r.t_plan_ns = (float)(t1 - t0);
+          r.t_grad_ns = (float)(t2 - t1);
+          r.t_step_ns = (float)(globaltimer() - t2);
+          r.t_grad_pass_ns = (float)(tg1 - t1);
+          r.t_grad_sync_ns = (float)(tg2 - t1);
+          r.t_step_pass_ns = (float)(ts1 - t2);
+          r.t_step_sync_ns = (float)(ts2 - t2);
+          r.replanned = replan;
+          r.grad_pairs = (long long)b.nnz_grad;
+          r.step_pairs = (long long)(b.nnz_total - pairs_before - b.nnz_grad);
+          r.grad_candidates = (long long)b.cand_grad;
+        }
+        if (!b.done) begin_iteration(cfg, b);
       }
     }
+    __syncthreads();
   }
+  if (blockIdx.x == 0 && tid == 0) publish(st, sm.b);
 }
 
-template <bool STEP>
-cudaError_t launch_dispatch(int dp, int color_mode, int nblocks, const SolveCfg* cfg,
-                            SolveState* st, double* partials, cudaGraphConditionalHandle cond,
-                            int use_cond, cudaStream_t s) {
-  dim3 grid(nblocks), block(kThreads);
-  if (color_mode == kColorNone || dp == 0) {
-    pair_pass_kernel<STEP, 0, kColorNone><<<grid, block, 0, s>>>(cfg, st, partials, cond, use_cond);
-  } else if (color_mode == kColorKernel) {
-    if (dp == 3) pair_pass_kernel<STEP, 3, kColorKernel><<<grid, block, 0, s>>>(cfg, st, partials, cond, use_cond);
-    else if (dp == 5) pair_pass_kernel<STEP, 5, kColorKernel><<<grid, block, 0, s>>>(cfg, st, partials, cond, use_cond);
-    else pair_pass_kernel<STEP, 8, kColorKernel><<<grid, block, 0, s>>>(cfg, st, partials, cond, use_cond);
-  } else {
-    if (dp == 3) pair_pass_kernel<STEP, 3, kColorDot><<<grid, block, 0, s>>>(cfg, st, partials, cond, use_cond);
-    else if (dp == 5) pair_pass_kernel<STEP, 5, kColorDot><<<grid, block, 0, s>>>(cfg, st, partials, cond, use_cond);
-    else pair_pass_kernel<STEP, 8, kColorDot><<<grid, block, 0, s>>>(cfg, st, partials, cond, use_cond);
-  }
-  return cudaGetLastError();
+template <int DP, int MODE>
+cudaError_t launch_solve_t(int nblocks, const SolveCfg* cfg, SolveState* st, double* partials,
+                           IterRecord* records, cudaStream_t s) {
+  void* args[] = {(void*)&cfg, (void*)&st, (void*)&partials, (void*)&records};
+  return cudaLaunchCooperativeKernel((const void*)solve_kernel<DP, MODE>, dim3(nblocks),
+                                     dim3(kThreads), args, 0, s);
 }
 
-// Sleeps about ns nanoseconds (bounded; used only to line up profiling events).
-__global__ void delay_kernel(unsigned ns) {
-  for (unsigned waited = 0; waited < ns; waited += 1000) __nanosleep(1000);
+template <int DP, int MODE>
+int blocks_per_sm_t() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<DP, MODE>, kThreads, 0) !=
+      cudaSuccess)
+    return 0;
+  return n;
 }
 
 }  // namespace
 
-cudaError_t launch_delay(unsigned ns, cudaStream_t s) {
-  delay_kernel<<<1, 1, 0, s>>>(ns);
-  return cudaGetLastError();
+cudaError_t launch_solve(int dp, int color_mode, int nblocks, const SolveCfg* cfg, SolveState* st,
+                         double* partials, IterRecord* records, cudaStream_t s) {
+  if (color_mode == kColorNone || dp == 0)
+    return launch_solve_t<0, kColorNone>(nblocks, cfg, st, partials, records, s);
+  if (color_mode == kColorKernel) {
+    if (dp == 3) return launch_solve_t<3, kColorKernel>(nblocks, cfg, st, partials, records, s);
+    if (dp == 5) return launch_solve_t<5, kColorKernel>(nblocks, cfg, st, partials, records, s);
+    return launch_solve_t<8, kColorKernel>(nblocks, cfg, st, partials, records, s);
+  }
+  if (dp == 3) return launch_solve_t<3, kColorDot>(nblocks, cfg, st, partials, records, s);
+  if (dp == 5) return launch_solve_t<5, kColorDot>(nblocks, cfg, st, partials, records, s);
+  return launch_solve_t<8, kColorDot>(nblocks, cfg, st, partials, records, s);
 }
 
-cudaError_t launch_init(const SolveCfg* cfg, SolveState* st, cudaGraphConditionalHandle cond,
-                        int use_cond, cudaStream_t s) {
-  init_kernel<<<1, 32, 0, s>>>(cfg, st, cond, use_cond);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_plan(const SolveCfg* cfg, SolveState* st, int ncl_launch, cudaStream_t s) {
-  const int blocks = (ncl_launch + kWarps - 1) / kWarps;
-  plan_kernel<<<blocks > 0 ? blocks : 1, kThreads, 0, s>>>(cfg, st);
-  chunk_scan_kernel<<<1, 1024, 0, s>>>(cfg, st);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pair_pass(bool step, int dp, int color_mode, int nblocks, const SolveCfg* cfg,
-                             SolveState* st, double* partials, cudaGraphConditionalHandle cond,
-                             int use_cond, cudaStream_t s) {
-  if (step) return launch_dispatch<true>(dp, color_mode, nblocks, cfg, st, partials, cond, use_cond, s);
-  return launch_dispatch<false>(dp, color_mode, nblocks, cfg, st, partials, cond, use_cond, s);
+int solve_blocks_per_sm(int dp, int color_mode) {
+  if (color_mode == kColorNone || dp == 0) return blocks_per_sm_t<0, kColorNone>();
+  if (color_mode == kColorKernel) {
+    if (dp == 3) return blocks_per_sm_t<3, kColorKernel>();
+    if (dp == 5) return blocks_per_sm_t<5, kColorKernel>();
+    return blocks_per_sm_t<8, kColorKernel>();
+  }
+  if (dp == 3) return blocks_per_sm_t<3, kColorDot>();
+  if (dp == 5) return blocks_per_sm_t<5, kColorDot>();
+  return blocks_per_sm_t<8, kColorDot>();
 }
 
 }  // namespace cvo
