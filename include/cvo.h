@@ -186,11 +186,47 @@ int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double
  * context runs; NULL for a NULL context. */
 void* cvo_stream(cvo_ctx* ctx);
 
+/* Gradient pass for callers that must not allocate device memory during the
+ * call: a program whose device memory is all owned by its own pool or fixed
+ * at start-up (a real-time loop with a frozen footprint, an embedding host
+ * that forbids allocation in its hot path) cannot use cvo_set_cloud, which
+ * copies clouds into library-allocated buffers. This entry point allocates
+ * nothing and needs no context. The paper has no counterpart: it is the
+ * all-pairs form of the gradient pass (every target point against every
+ * source point, with the same cutoff, label product and FP32 pair
+ * arithmetic as cvo_eval), so its cost grows with n * m.
+ *
+ * Inputs are device pointers on the current device: d_x (n x 3 float32) and
+ * d_fx (n x feat_dim) the target, d_z (m x 3) and d_fz (m x feat_dim) the
+ * source (features may be NULL when feat_dim is 0 or color_mode is NONE).
+ * params supplies sigma, kcut, color_mode, ell_color, color_scale, a2, b2 and
+ * feat_dim; P (host, row-major 4x4) the pose; ell the lengthscale. The result
+ * is written to d_out, a device array of 8 doubles: F, the metric gradient
+ * (omega, v) as in cvo_eval_result.grad6, and the number of kept pairs. The
+ * kernels run on `stream` (NULL: the default stream) and the call returns
+ * without waiting for them.
+ *
+ * Scratch: block partials live in a fixed 32 KB array in the library's
+ * device memory (512 slots), which every GPU that loads the library holds
+ * until the process exits. Each call writes every slot it reads, so nothing
+ * carries over between calls, but all calls on one device share the array:
+ * calls whose kernels overlap on the GPU (different streams, or different
+ * host threads) race and must be serialised by the caller. The first call on
+ * each device looks up the array's device address; make that first call
+ * before any stream capture. Sizes outside 1 <= n, m <= 2^22 return
+ * CVO_ERR_INVALID_ARG; so do NULL pointers and invalid parameters. The detail
+ * message of a failed call is returned by cvo_last_error(NULL) on the same
+ * host thread. */
+int cvo_eval_gradient_static(const float* d_x, const float* d_fx, int64_t n, const float* d_z,
+                             const float* d_fz, int64_t m, const cvo_params* params,
+                             const double P[16], double ell, double* d_out, void* stream);
+
 /* Name of a status code (static string). */
 const char* cvo_strerror(int status);
 
 /* Detail message of the last failed call on this context (static until the
- * next call on the context; "" if none). */
+ * next call on the context; "" if none). With ctx == NULL: the message of the
+ * last failed context-free call (cvo_eval_gradient_static) on this thread. */
 const char* cvo_last_error(cvo_ctx* ctx);
 
 #ifdef __cplusplus

@@ -38,7 +38,7 @@ CVO_MAX_FEAT = 8
 # every entry point declared in include/cvo.h
 EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
            "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile", "cvo_stream",
-           "cvo_strerror", "cvo_last_error")
+           "cvo_eval_gradient_static", "cvo_strerror", "cvo_last_error")
 
 
 class CvoUnavailable(RuntimeError):
@@ -123,6 +123,10 @@ def load_library(path: str = LIB_PATH):
                                           ctypes.POINTER(cvo_iter_profile), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]
         lib.cvo_align_profile.restype = ctypes.c_int
+        lib.cvo_eval_gradient_static.argtypes = [vp, vp, ctypes.c_int64, vp, vp, ctypes.c_int64,
+                                                 ctypes.POINTER(cvo_params), dp, ctypes.c_double,
+                                                 vp, vp]
+        lib.cvo_eval_gradient_static.restype = ctypes.c_int
         lib.cvo_stream.argtypes = [vp]
         lib.cvo_stream.restype = ctypes.c_void_p
         lib.cvo_strerror.argtypes = [ctypes.c_int]
@@ -246,6 +250,30 @@ def cvo_align_profile(ctx, target: int, source: int, P0=None, max_records: int =
     records = [{k: getattr(recs[i], k) for k, _ in cvo_iter_profile._fields_}
                for i in range(nrec.value)]
     return out, stats, records
+
+
+def cvo_eval_gradient_static(x, fx, z, fz, params: cvo_params, P, ell: float, out,
+                             stream=None) -> None:
+    """Allocation-free gradient pass on device tensors (torch CUDA float32, or
+    raw device addresses). out: a device tensor of 8 float64 (F, grad6, kept
+    pairs), written asynchronously on `stream` (default: torch's current
+    stream)."""
+    def addr(t):
+        if t is None:
+            return None
+        return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
+
+    n = int(x.shape[0])
+    m = int(z.shape[0])
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _, pp = _pose(P)
+    code = load_library().cvo_eval_gradient_static(addr(x), addr(fx), n, addr(z), addr(fz), m,
+                                                   ctypes.byref(params), pp, float(ell), addr(out),
+                                                   stream if stream else None)
+    if code != CVO_OK:
+        raise CvoError(code, load_library().cvo_last_error(None).decode())
 
 
 def cvo_stream(ctx) -> int:

@@ -20,6 +20,8 @@
 
 using namespace cvo;
 
+const char* cvo_static_last_error();   // noalloc.cu
+
 namespace {
 
 struct Grid {
@@ -513,7 +515,7 @@ const char* cvo_strerror(int s) {
   }
 }
 
-const char* cvo_last_error(cvo_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+const char* cvo_last_error(cvo_ctx* ctx) { return ctx ? ctx->err.c_str() : cvo_static_last_error(); }
 
 int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cvo_ctx** out) {
   if (!out) return CVO_ERR_INVALID_ARG;
