@@ -232,7 +232,7 @@ def run_cvo(args, world, rank, local):
     clocks = clk.summary()
     pairs = sum(o[1]["pair_evals"] for o in outs)
     iters = [o[1]["iters"] for o in outs]
-    launches = sum(1 + 4 * it for it in iters)  # init + (plan, chunk split, gradient, step) per iteration
+    launches = len(iters)   # one solve_kernel launch per step
     P_final = outs[-1][0]
 
     # end to end through the public API from host buffers: upload both clouds
@@ -251,22 +251,18 @@ def run_cvo(args, world, rank, local):
     import ctypes
     d2h = 16 * 8 + ctypes.sizeof(cvo.cvo_stats)
 
-    # per-kernel CUDA-event timing of the same solve (host-driven loop)
+    # roofline of the solve kernel (the only kernel of a timed step): algorithmic
+    # FP32 flops of the kept pairs of one solve over the CUDA-event time per
+    # solve; the per-phase split comes from the kernel's own timestamps
     _, pst, recs = ctx.align_profile(ht, hs)
     fpp = flops_per_pair(D)
-    grad_ms = sum(r["grad_ms"] for r in recs)
-    step_ms = sum(r["step_ms"] for r in recs)
     grad_pairs = sum(r["grad_pairs"] for r in recs)
     step_pairs = sum(r["step_pairs"] for r in recs)
     cand = sum(r["grad_candidates"] for r in recs)
-    passes = {
-        "grad": {"achieved": grad_pairs * fpp["grad"] / (grad_ms * 1e-3) / 1e12,
-                 "ms_per_launch": grad_ms / len(recs), "pairs_per_launch": grad_pairs / len(recs)},
-        "step": {"achieved": step_pairs * fpp["step"] / (step_ms * 1e-3) / 1e12,
-                 "ms_per_launch": step_ms / len(recs), "pairs_per_launch": step_pairs / len(recs)},
-    }
-    dom = "step" if step_ms >= grad_ms else "grad"
-    achieved = passes[dom]["achieved"]
+    flops_per_solve = grad_pairs * fpp["grad"] + step_pairs * fpp["step"]
+    achieved = flops_per_solve / (ms / args.steps * 1e-3) / 1e12
+    phases = {k: sum(r[k] for r in recs) for k in ("plan_ms", "grad_ms", "step_ms")}
+    traffic = recorded_traffic("solve_kernel")
 
     # max over ranks
     total_ms = ms
@@ -302,11 +298,12 @@ def run_cvo(args, world, rank, local):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": f"pair_pass_kernel<{dom}>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "solve_kernel", "achieved": achieved,
                      "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
-                     "traffic": None,
+                     "traffic": traffic,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                     "passes": passes},
+                     "flops_per_launch": flops_per_solve,
+                     "phase_ms_per_solve": phases},
         "clocks": clocks,
     }
     if not args.no_cpu_baseline and world == 1:
@@ -319,6 +316,27 @@ def run_cvo(args, world, rank, local):
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_1904_02266_gb300", "csrc", "pair_kernels.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md")):
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256_16") == digest and "dram_bytes_per_launch" in fields:
+            try:
+                return float(fields["dram_bytes_per_launch"])
+            except ValueError:
+                return None
+    return None
 
 
 def synth_pose_err(P, Pref):
