@@ -105,6 +105,7 @@ struct SolveState {
   unsigned long long nnz_pass[2], cand_pass[2];
   unsigned long long nnz_eval, cand_eval;   // gradient pass of the last iteration
   unsigned int bar_count, bar_gen;          // grid barrier (zeroed before each launch)
+  double red_sums[10];                      // pass totals published by the barrier's last block
 };
 
 // Per-iteration record of a profiled solve (device timestamps).

@@ -37,6 +37,11 @@
 
 #include "cvo_internal.cuh"
 
+// Resident blocks per SM the solve kernel is compiled for (register budget).
+#ifndef CVO_SOLVE_MIN_BLOCKS
+#define CVO_SOLVE_MIN_BLOCKS 2
+#endif
+
 namespace cvo {
 
 namespace {
@@ -151,7 +156,8 @@ __device__ void begin_iteration(const SolveCfg* cfg, BlockCtx& b) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) dt += (T[i] - b.Tp[i]) * (T[i] - b.Tp[i]);
     // |dR z + dT| <= |dR|_F |z| + |dT| for every source point, |z| <= r_src
-    const double drift = sqrt(dr) * cfg->src_radius + sqrt(dt) + 1e-6 * need;
+    const double drift = ((double)sqrtf((float)dr) * cfg->src_radius + (double)sqrtf((float)dt)) *
+                             (1.0 + 1e-5) + 1e-6 * need;
     replan = (need + drift > b.r_plan) || (b.r_plan > kLoose * (need + drift));
   }
   b.level = ic.level;
@@ -193,7 +199,8 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
       }
     }
   } else {
-    const double B = c2 / c3, C = c1 / c3, D = c0 / c3;
+    const double r3 = 1.0 / c3;
+    const double B = c2 * r3, C = c1 * r3, D = c0 * r3;
     const double B3 = B * (1.0 / 3.0);
     const double p = C - B * B3;
     const double q = (2.0 / 27.0) * B * B * B - B3 * C + D;
@@ -401,6 +408,82 @@ __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag) {
   return *s_flag != 0;
 }
 
+// Fixed-order FP64 sum of all block partials. Warp w sums values w and w + 8:
+// lane l adds blocks l, l + 32, ... (all loads issued first, then a pairwise
+// tree), then a shuffle tree across lanes. Results land in out[] (shared).
+// Must be called by every thread of the block.
+__device__ void reduce_partials(const double* partials, int nvals, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kMaxPerLane = 16;   // blocks per lane: up to 512 blocks
+  for (int i = warp; i < nvals; i += kWarps) {
+    double v[kMaxPerLane];
+#pragma unroll
+    for (int q = 0; q < kMaxPerLane; ++q) {
+      const int b = lane + 32 * q;
+      v[q] = b < (int)gridDim.x ? __ldcg(&partials[(size_t)b * kPartialStride + i]) : 0.0;
+    }
+#pragma unroll
+    for (int w = kMaxPerLane / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int q = 0; q < w; ++q) v[q] += v[q + w];
+    const double s = warp_sum_d(v[0]);
+    if (lane == 0) out[i] = s;
+  }
+  __syncthreads();
+}
+
+// Barrier that also reduces the pass: the last block to arrive sums all block
+// partials in FP64 (fixed order, all its threads), publishes the totals and
+// then releases the others, which read the totals. Every thread of every block
+// gets the totals in sums[]. Bounded like grid_sync.
+template <class Smem>
+__device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const double* partials,
+                                 int nvals) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    sm.last = (arrived == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  int ok = 1;
+  const unsigned g = gen;
+  if (sm.last) {
+    reduce_partials(partials, nvals, sm.sums);
+    if (threadIdx.x < (unsigned)nvals) st->red_sums[threadIdx.x] = sm.sums[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicExch(&st->bar_gen, g + 1);
+    }
+  } else {
+    if (threadIdx.x == 0) {
+      unsigned spins = 0;
+      while (ld_acquire(&st->bar_gen) == g) {
+        if (++spins > kSpinLimit) {
+          ok = 0;
+          atomicOr(&st->status, (int)kStatusTimeout);
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+      sm.flag = ok;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)nvals) sm.sums[threadIdx.x] = __ldcg(&st->red_sums[threadIdx.x]);
+  }
+  gen = g + 1;
+  if (threadIdx.x == 0) {
+    if (sm.last) sm.flag = 1;
+    if (ld_acquire((const unsigned*)&st->status) & kStatusTimeout) sm.flag = 0;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+
 // Plan of one cluster (one warp): transform its points, bounding box, cell
 // rows within the plan radius -> segments, candidate count.
 __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState* st, int c,
@@ -514,7 +597,7 @@ struct SolveSmem {
   long long bnd_base[2 * kWarps];   // work offset of the group holding each warp boundary
   int bnd_group[2 * kWarps];
   double sums[10];
-  int flag;
+  int flag, last;
   BlockCtx b;
 };
 
@@ -853,30 +936,6 @@ __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* pa
   }
 }
 
-// Fixed-order FP64 sum of all block partials. Warp w sums values w and w + 8:
-// lane l adds blocks l, l + 32, ... (all loads issued first, then a pairwise
-// tree), then a shuffle tree across lanes. Results land in out[] (shared).
-// Must be called by every thread of the block.
-__device__ void reduce_partials(const double* partials, int nvals, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kMaxPerLane = 16;   // blocks per lane: up to 512 blocks
-  for (int i = warp; i < nvals; i += kWarps) {
-    double v[kMaxPerLane];
-#pragma unroll
-    for (int q = 0; q < kMaxPerLane; ++q) {
-      const int b = lane + 32 * q;
-      v[q] = b < (int)gridDim.x ? __ldcg(&partials[(size_t)b * kPartialStride + i]) : 0.0;
-    }
-#pragma unroll
-    for (int w = kMaxPerLane / 2; w > 0; w >>= 1)
-#pragma unroll
-      for (int q = 0; q < w; ++q) v[q] += v[q + w];
-    const double s = warp_sum_d(v[0]);
-    if (lane == 0) out[i] = s;
-  }
-  __syncthreads();
-}
-
 __device__ void publish(SolveState* st, const BlockCtx& b) {
   for (int i = 0; i < 16; ++i) st->P[i] = b.P[i];
   for (int i = 0; i < 6; ++i) st->xi[i] = b.xi[i];
@@ -899,7 +958,7 @@ __device__ void publish(SolveState* st, const BlockCtx& b) {
 
 // The whole solve (or one evaluation) in one cooperative launch.
 template <int DP, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
 solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
              double* __restrict__ partials, IterRecord* __restrict__ records) {
   constexpr int DPS = DP > 0 ? DP : 1;
@@ -959,18 +1018,16 @@ solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
     // ---- gradient pass ----
     run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g);
     if (stamp) tg1 = globaltimer();
-    if (!grid_sync(st, gen, &sm.flag)) break;
+    if (!grid_sync_reduce(st, gen, sm, part_g, 9)) break;
     if (stamp) tg2 = globaltimer();
-    reduce_partials(part_g, 9, sm.sums);
     if (tid == 0) finish_gradient(cfg, sm.b, sm.sums);
     __syncthreads();
     if (stamp) t2 = globaltimer();
     // ---- step pass ----
     run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s);
     if (stamp) ts1 = globaltimer();
-    if (!grid_sync(st, gen, &sm.flag)) break;
+    if (!grid_sync_reduce(st, gen, sm, part_s, 7)) break;
     if (stamp) ts2 = globaltimer();
-    reduce_partials(part_s, 7, sm.sums);
     {
       if (tid == 0) {
         BlockCtx& b = sm.b;
