@@ -90,6 +90,9 @@ typedef struct {
                               capped so a cluster spans at most 8 x 8 cell rows; 2.0 */
     int cost_chunk;        /* work split: per-chunk overhead in pair-test units; 24 */
     int cost_cluster;      /* work split: cost of staging one cluster in pair-test units; 64 */
+    double team_factor;    /* batches and served requests: a pair's team gets about
+                              team_factor * (its share of the estimated pair work) of the
+                              blocks, at least one; 6.0 */
 } cvo_params;
 
 /* One evaluation at a fixed pose (cvo_eval). */
@@ -115,6 +118,8 @@ typedef struct {
     int64_t pair_evals;   /* kept pairs summed over every gradient and step pass */
     int64_t candidates;   /* candidate pairs visited over every pass */
     int status;           /* CVO_OK or the error that ended the solve */
+    double device_ms;     /* device time of the solve (global timer, from the moment all
+                             blocks of its team had started to the published result) */
 } cvo_stats;
 
 /* Fill *p with the defaults listed in cvo_params. */
@@ -185,6 +190,53 @@ int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double
 /* The context's CUDA stream (cudaStream_t), on which every kernel of the
  * context runs; NULL for a NULL context. */
 void* cvo_stream(cvo_ctx* ctx);
+
+/* ---- batches: many uneven pairs in one persistent launch ---------------- */
+
+typedef struct cvo_batch cvo_batch;
+
+/* Describe a batch of n independent solves, pair i aligning source[i] to
+ * target[i] (resident cloud handles; a handle may appear in several pairs).
+ * ell0 (may be NULL) gives each pair its own initial lengthscale for the
+ * context's schedule. team_sizes (may be NULL) fixes how many blocks solve
+ * each pair; otherwise the library estimates each pair's kept-pair work from
+ * the point counts, the target's extent and the schedule, and gives it
+ * max(1, ceil(team_factor * share * blocks)) blocks. Pairs are queued largest
+ * first; blocks of one persistent cooperative kernel claim them as they come
+ * free, so small pairs fill in around large ones. The call builds every cell
+ * list, cluster set and per-pair plan the solves need and captures the launch
+ * (pose upload, kernel, result download) in a CUDA graph. The clouds of a
+ * batch cannot be released (CVO_ERR_BUSY) until the batch is destroyed.
+ * Errors: CVO_ERR_INVALID_ARG (n < 1, NULL arrays, team size outside
+ * [1, blocks], ell0 <= 0), CVO_ERR_NOT_FOUND (unknown handle),
+ * CVO_ERR_OUT_OF_BUDGET. */
+int cvo_batch_create(cvo_ctx* ctx, int n, const int32_t* targets, const int32_t* sources,
+                     const double* ell0, const int32_t* team_sizes, cvo_batch** out);
+
+/* Run every solve of the batch from the poses P0 (n row-major 4x4 doubles).
+ * Synchronous. P_out receives n final poses, stats (may be NULL) n records
+ * whose status field is that pair's own outcome. Each pair runs the same
+ * iteration as cvo_align (same schedule, step rule and stopping test); only
+ * the order of the FP64 sums over blocks differs with the team size.
+ * Returns the first failing pair's status, else CVO_OK. */
+int cvo_batch_run(cvo_ctx* ctx, cvo_batch* batch, const double* P0, double* P_out,
+                  cvo_stats* stats);
+
+typedef struct {
+    int pairs;          /* pairs in the batch */
+    int blocks;         /* blocks of the persistent launch */
+    int graph;          /* 1 if the launch is replayed from a captured CUDA graph */
+    int max_team;       /* largest team */
+    int64_t bytes;      /* device memory held by the batch (plans, states, queue) */
+} cvo_batch_info;
+
+/* Shape of a batch; team_sizes (may be NULL) receives the n team sizes in
+ * the caller's pair order. */
+int cvo_batch_get_info(cvo_ctx* ctx, const cvo_batch* batch, cvo_batch_info* info,
+                       int32_t* team_sizes);
+
+/* Free the batch's plans, states and graph. */
+int cvo_batch_destroy(cvo_ctx* ctx, cvo_batch* batch);
 
 /* Gradient pass for callers that must not allocate device memory during the
  * call: a program whose device memory is all owned by its own pool or fixed

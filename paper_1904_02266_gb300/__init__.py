@@ -38,6 +38,7 @@ CVO_MAX_FEAT = 8
 # every entry point declared in include/cvo.h
 EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
            "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile", "cvo_stream",
+           "cvo_batch_create", "cvo_batch_run", "cvo_batch_get_info", "cvo_batch_destroy",
            "cvo_eval_gradient_static", "cvo_strerror", "cvo_last_error")
 
 
@@ -61,7 +62,8 @@ class cvo_params(ctypes.Structure):
                 ("eps_pose", ctypes.c_double), ("eps_grad", ctypes.c_double),
                 ("step_order", ctypes.c_int), ("feat_dim", ctypes.c_int),
                 ("cell_factor", ctypes.c_double), ("cluster_factor", ctypes.c_double),
-                ("cost_chunk", ctypes.c_int), ("cost_cluster", ctypes.c_int)]
+                ("cost_chunk", ctypes.c_int), ("cost_cluster", ctypes.c_int),
+                ("team_factor", ctypes.c_double)]
 
 
 class cvo_eval_result(ctypes.Structure):
@@ -75,7 +77,8 @@ class cvo_stats(ctypes.Structure):
                 ("fallback_steps", ctypes.c_int), ("no_ascent_steps", ctypes.c_int),
                 ("final_ell", ctypes.c_double), ("F_last", ctypes.c_double),
                 ("t_last", ctypes.c_double), ("pair_evals", ctypes.c_int64),
-                ("candidates", ctypes.c_int64), ("status", ctypes.c_int)]
+                ("candidates", ctypes.c_int64), ("status", ctypes.c_int),
+                ("device_ms", ctypes.c_double)]
 
 
 class cvo_iter_profile(ctypes.Structure):
@@ -86,6 +89,11 @@ class cvo_iter_profile(ctypes.Structure):
                 ("grad_pairs", ctypes.c_int64),
                 ("step_pairs", ctypes.c_int64), ("grad_candidates", ctypes.c_int64),
                 ("step_candidates", ctypes.c_int64)]
+
+
+class cvo_batch_info(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int), ("blocks", ctypes.c_int), ("graph", ctypes.c_int),
+                ("max_team", ctypes.c_int), ("bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -127,6 +135,12 @@ def load_library(path: str = LIB_PATH):
                                                  ctypes.POINTER(cvo_params), dp, ctypes.c_double,
                                                  vp, vp]
         lib.cvo_eval_gradient_static.restype = ctypes.c_int
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.cvo_batch_create.argtypes = [vp, ctypes.c_int, i32p, i32p, dp, i32p,
+                                         ctypes.POINTER(vp)]
+        lib.cvo_batch_run.argtypes = [vp, vp, dp, dp, ctypes.POINTER(cvo_stats)]
+        lib.cvo_batch_get_info.argtypes = [vp, vp, ctypes.POINTER(cvo_batch_info), i32p]
+        lib.cvo_batch_destroy.argtypes = [vp, vp]
         lib.cvo_stream.argtypes = [vp]
         lib.cvo_stream.restype = ctypes.c_void_p
         lib.cvo_strerror.argtypes = [ctypes.c_int]
@@ -134,7 +148,8 @@ def load_library(path: str = LIB_PATH):
         lib.cvo_last_error.argtypes = [vp]
         lib.cvo_last_error.restype = ctypes.c_char_p
         for name in ("cvo_create", "cvo_destroy", "cvo_set_cloud", "cvo_release_cloud",
-                     "cvo_eval", "cvo_align"):
+                     "cvo_eval", "cvo_align", "cvo_batch_create", "cvo_batch_run",
+                     "cvo_batch_get_info", "cvo_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -252,6 +267,56 @@ def cvo_align_profile(ctx, target: int, source: int, P0=None, max_records: int =
     return out, stats, records
 
 
+def _i32(a):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def cvo_batch_create(ctx, targets, sources, ell0=None, team_sizes=None):
+    """Batch of len(targets) solves; returns the opaque batch pointer."""
+    t, tp = _i32(targets)
+    s, sp = _i32(sources)
+    if t.shape != s.shape:
+        raise ValueError("targets and sources differ in length")
+    e = None if ell0 is None else np.ascontiguousarray(np.asarray(ell0, dtype=np.float64))
+    g = None if team_sizes is None else _i32(team_sizes)
+    out = ctypes.c_void_p()
+    _check(ctx, load_library().cvo_batch_create(
+        ctx, int(t.size), tp, sp,
+        None if e is None else e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        None if g is None else g[1], ctypes.byref(out)))
+    return out
+
+
+def cvo_batch_run(ctx, batch, P0):
+    """P0: (n, 4, 4). Returns (poses (n, 4, 4), list of per-pair stats dicts)."""
+    p0 = np.ascontiguousarray(np.asarray(P0, dtype=np.float64))
+    n = p0.shape[0]
+    out = np.zeros((n, 4, 4))
+    st = (cvo_stats * n)()
+    code = load_library().cvo_batch_run(ctx, batch,
+                                        p0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st)
+    stats = [{k: getattr(st[i], k) for k, _ in cvo_stats._fields_} for i in range(n)]
+    _check(ctx, code)
+    return out, stats
+
+
+def cvo_batch_get_info(ctx, batch, n: int | None = None) -> dict:
+    info = cvo_batch_info()
+    _check(ctx, load_library().cvo_batch_get_info(ctx, batch, ctypes.byref(info), None))
+    teams = np.zeros(info.pairs, dtype=np.int32)
+    _check(ctx, load_library().cvo_batch_get_info(
+        ctx, batch, None, teams.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    d = {k: getattr(info, k) for k, _ in cvo_batch_info._fields_}
+    d["teams"] = teams
+    return d
+
+
+def cvo_batch_destroy(ctx, batch) -> None:
+    _check(ctx, load_library().cvo_batch_destroy(ctx, batch))
+
+
 def cvo_eval_gradient_static(x, fx, z, fz, params: cvo_params, P, ell: float, out,
                              stream=None) -> None:
     """Allocation-free gradient pass on device tensors (torch CUDA float32, or
@@ -289,6 +354,32 @@ def cvo_last_error(ctx) -> str:
     return load_library().cvo_last_error(ctx).decode()
 
 
+class Batch:
+    """Many pair solves in one persistent launch (cvo_batch_*)."""
+
+    def __init__(self, ctx: "Context", targets, sources, ell0=None, team_sizes=None):
+        self._ctx = ctx
+        self.n = len(targets)
+        self.ptr = cvo_batch_create(ctx.ctx, targets, sources, ell0, team_sizes)
+
+    def run(self, P0):
+        return cvo_batch_run(self._ctx.ctx, self.ptr, P0)
+
+    def info(self) -> dict:
+        return cvo_batch_get_info(self._ctx.ctx, self.ptr)
+
+    def close(self) -> None:
+        if self.ptr and self._ctx.ctx:
+            cvo_batch_destroy(self._ctx.ctx, self.ptr)
+        self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Context:
     """One library context: clouds, cached cell lists and solve plans on one GPU."""
 
@@ -316,6 +407,9 @@ class Context:
 
     def align_profile(self, target: int, source: int, P0=None, max_records: int = 1000):
         return cvo_align_profile(self.ctx, target, source, P0, max_records)
+
+    def batch(self, targets, sources, ell0=None, team_sizes=None) -> "Batch":
+        return Batch(self, targets, sources, ell0, team_sizes)
 
     @property
     def stream(self) -> int:

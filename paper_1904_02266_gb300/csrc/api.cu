@@ -1,7 +1,8 @@
 // Host runtime behind the C ABI in include/cvo.h: contexts, clouds, cached
-// target cell lists, solve plans and the CUDA graph that runs a whole solve on
-// the device (Problem 1 iterated by a while-conditional graph node, no host
-// round trip per iteration).
+// target cell lists, solve plans, and the launches that run a whole solve on
+// the device (Problem 1 iterated inside one persistent kernel, no host round
+// trip per iteration): one pair per launch, or many uneven pairs in one
+// queue-driven launch replayed from a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,6 +56,7 @@ struct Cloud {
   std::vector<Grid> grids;
   std::vector<Clusters> clusters;
   size_t bytes = 0;
+  int refs = 0;           // batches that use the cloud
 };
 
 struct Plan {
@@ -77,7 +79,33 @@ struct Plan {
   size_t bytes = 0;
 };
 
+// Queue control of a batch launch (device memory): the control words, the
+// slot counter and the kernel status, the last two zeroed before each launch.
+struct BatchCtl {
+  QueueCtl q;
+  unsigned long long head;
+  int kstatus;
+  int pad;
+};
+
 }  // namespace
+
+struct cvo_batch {
+  int n = 0;
+  int nblocks = 0;
+  int dp = 0, color_mode = 0;
+  std::vector<Plan*> plans;       // caller order
+  std::vector<int32_t> tgt, src;  // caller order
+  std::vector<int> team;          // caller order
+  std::vector<int> order;         // queue position -> caller index (largest work first)
+  SolveState* d_states = nullptr; // queue order
+  SolveState* h_states = nullptr; // pinned, queue order
+  QueueEntry* d_entries = nullptr;
+  BatchCtl* d_ctl = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  size_t bytes = 0;
+};
 
 struct cvo_ctx {
   int device = 0;
@@ -88,6 +116,7 @@ struct cvo_ctx {
   cudaStream_t cap_stream = nullptr;
   std::vector<Cloud*> clouds;
   std::map<std::pair<int, int>, Plan*> plans;
+  std::vector<cvo_batch*> batches;
   Plan* eval_plan = nullptr;      // reused by cvo_eval
   SolveState* h_state = nullptr;  // pinned
   CloudStats* d_stats = nullptr;
@@ -465,6 +494,8 @@ int run_solve(cvo_ctx* ctx, Plan* p, const double P0[16], bool records) {
   return CVO_OK;
 }
 
+void destroy_batch(cvo_ctx* ctx, cvo_batch* b);
+
 int check_pose(cvo_ctx* ctx, const double* P) {
   if (!P) return fail(ctx, CVO_ERR_INVALID_ARG, "pose pointer is NULL");
   for (int i = 0; i < 16; ++i)
@@ -499,6 +530,7 @@ void cvo_params_default(cvo_params* p) {
   p->cluster_factor = 2.0;
   p->cost_chunk = 24;
   p->cost_cluster = 64;
+  p->team_factor = 6.0;
 }
 
 const char* cvo_strerror(int s) {
@@ -533,7 +565,8 @@ int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cv
                   (p.color_mode != CVO_COLOR_DOT || p.color_scale > 0) &&
                   p.cell_factor >= 0.5 && p.cell_factor <= 8.0 && std::isfinite(p.ell0) &&
                   p.cluster_factor > 0.0 && p.cluster_factor <= 8.0 && p.cost_chunk >= 0 &&
-                  p.cost_chunk <= 4096 && p.cost_cluster >= 0 && p.cost_cluster <= 65536;
+                  p.cost_chunk <= 4096 && p.cost_cluster >= 0 && p.cost_cluster <= 65536 &&
+                  p.team_factor > 0.0 && p.team_factor <= 1024.0;
   if (!ok) return CVO_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -562,6 +595,7 @@ int cvo_destroy(cvo_ctx* ctx) {
   if (!ctx) return CVO_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  while (!ctx->batches.empty()) destroy_batch(ctx, ctx->batches.back());
   for (auto& kv : ctx->plans) free_plan(ctx, kv.second);
   ctx->plans.clear();
   free_plan(ctx, ctx->eval_plan);
@@ -681,6 +715,7 @@ int cvo_release_cloud(cvo_ctx* ctx, int32_t handle) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   Cloud* c = get_cloud(ctx, handle);
   if (!c) return fail(ctx, CVO_ERR_NOT_FOUND, "unknown cloud handle");
+  if (c->refs > 0) return fail(ctx, CVO_ERR_BUSY, "cloud is used by a batch");
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
@@ -763,6 +798,7 @@ void fill_stats(const SolveState* hs, cvo_stats* stats) {
     stats->pair_evals = (int64_t)hs->nnz_total;
     stats->candidates = (int64_t)hs->cand_total;
     stats->status = hs->status;
+    stats->device_ms = (double)(hs->t_end_ns - hs->t_begin_ns) * 1e-6;
   }
 }
 
@@ -826,5 +862,266 @@ int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double
 }
 
 void* cvo_stream(cvo_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+}  // extern "C"
+
+namespace {
+
+// Estimated kept pairs of a whole solve, for team sizing: the source points
+// times the target's points per unit area (its bounding box read as a
+// surface: the sum of the products of pairs of extents) times the cutoff
+// disc area, summed over the schedule, two passes per iteration.
+double pair_work(const cvo_params& prm, const Cloud* t, const Cloud* s,
+                 const std::vector<double>& ells) {
+  double e[3];
+  for (int a = 0; a < 3; ++a) e[a] = std::max(0.0, (double)t->hi[a] - (double)t->lo[a]);
+  const double emax = std::max(e[0], std::max(e[1], e[2]));
+  const double area = std::max(e[0] * e[1] + e[0] * e[2] + e[1] * e[2],
+                               std::max(1e-3 * emax * emax, 1e-6));
+  const double dens = (double)t->n / area;
+  const double pi = 3.14159265358979323846;
+  double disc = 0.0;
+  for (double ell : ells) {
+    const double rc = cutoff_radius(prm, ell);
+    disc += pi * rc * rc;
+  }
+  return 2.0 * (double)s->n * std::min((double)t->n, dens * disc / (double)ells.size()) *
+         (double)ells.size();
+}
+
+// The device work of one batch run on stream st: poses and zeroed states up,
+// queue counters reset, the persistent launch, states down.
+cudaError_t record_batch_launch(cvo_batch* b, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(b->d_states, b->h_states, sizeof(SolveState) * b->n,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(&b->d_ctl->head, 0, sizeof(unsigned long long) + sizeof(int), st);
+  if (e == cudaSuccess)
+    e = launch_queue(b->dp, b->color_mode, b->nblocks, b->d_entries, &b->d_ctl->q,
+                     &b->d_ctl->head, &b->d_ctl->kstatus, 0ull, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_states, b->d_states, sizeof(SolveState) * b->n,
+                        cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
+void destroy_batch(cvo_ctx* ctx, cvo_batch* b) {
+  if (!b) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (Plan* p : b->plans) free_plan(ctx, p);
+  for (size_t i = 0; i < b->tgt.size(); ++i) {
+    if (Cloud* c = get_cloud(ctx, b->tgt[i])) c->refs -= 1;
+    if (Cloud* c = get_cloud(ctx, b->src[i])) c->refs -= 1;
+  }
+  cudaFree(b->d_states);
+  cudaFree(b->d_entries);
+  cudaFree(b->d_ctl);
+  if (b->h_states) cudaFreeHost(b->h_states);
+  release_bytes(ctx, b->bytes);
+  ctx->batches.erase(std::remove(ctx->batches.begin(), ctx->batches.end(), b),
+                     ctx->batches.end());
+  delete b;
+}
+
+int status_code(int bits) {
+  if (bits & kStatusTimeout) return CVO_ERR_TIMEOUT;
+  if (bits != 0) return CVO_ERR_INTERNAL;
+  return CVO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cvo_batch_create(cvo_ctx* ctx, int n, const int32_t* targets, const int32_t* sources,
+                     const double* ell0, const int32_t* team_sizes, cvo_batch** out) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL batch pointer");
+  *out = nullptr;
+  if (n < 1 || !targets || !sources)
+    return fail(ctx, CVO_ERR_INVALID_ARG, "a batch needs n >= 1 and target/source arrays");
+  for (int i = 0; i < n; ++i) {
+    if (!get_cloud(ctx, targets[i]) || !get_cloud(ctx, sources[i]))
+      return fail(ctx, CVO_ERR_NOT_FOUND, "unknown cloud handle in batch");
+    if (ell0 && !(ell0[i] > 0.0 && std::isfinite(ell0[i])))
+      return fail(ctx, CVO_ERR_INVALID_ARG, "ell0 must be > 0");
+  }
+  CK(cudaSetDevice(ctx->device));
+  const Cloud* s0 = get_cloud(ctx, sources[0]);
+  const int per_sm = solve_blocks_per_sm(s0->dp, ctx->prm.color_mode);
+  if (per_sm <= 0) return fail(ctx, CVO_ERR_CUDA, "solve kernel cannot be resident");
+  const int nblocks = std::min(per_sm * ctx->sms, 512);
+  if (team_sizes)
+    for (int i = 0; i < n; ++i)
+      if (team_sizes[i] < 1 || team_sizes[i] > nblocks)
+        return fail(ctx, CVO_ERR_INVALID_ARG, "team size outside [1, blocks]");
+  cvo_batch* b = new cvo_batch();
+  b->n = n;
+  b->nblocks = nblocks;
+  b->dp = s0->dp;
+  b->color_mode = ctx->prm.color_mode;
+  b->plans.assign(n, nullptr);
+  b->tgt.assign(targets, targets + n);
+  b->src.assign(sources, sources + n);
+  for (int i = 0; i < n; ++i) {
+    get_cloud(ctx, targets[i])->refs += 1;
+    get_cloud(ctx, sources[i])->refs += 1;
+  }
+  ctx->batches.push_back(b);
+  auto bail = [&](int rc) {
+    destroy_batch(ctx, b);
+    return rc;
+  };
+  // one plan per pair: the teams run at the same time, so no two pairs may
+  // share work buffers even when they name the same clouds
+  std::vector<double> work(n);
+  const int iters = std::max(1, ctx->prm.max_iters);
+  for (int i = 0; i < n; ++i) {
+    cvo_params prm = ctx->prm;
+    if (ell0) prm.ell0 = ell0[i];
+    std::vector<double> ells = ell_schedule(prm, iters);
+    Cloud* t = get_cloud(ctx, targets[i]);
+    Cloud* s = get_cloud(ctx, sources[i]);
+    Plan* p = new Plan();
+    p->tgt = targets[i];
+    p->src = sources[i];
+    b->plans[i] = p;
+    int rc = configure_plan(ctx, p, t, s, ells, kModeAlign);
+    if (rc != CVO_OK) return bail(rc);
+    work[i] = pair_work(ctx->prm, t, s, ells);
+  }
+  double total = 0.0;
+  for (double w : work) total += w;
+  b->team.resize(n);
+  for (int i = 0; i < n; ++i) {
+    if (team_sizes) {
+      b->team[i] = team_sizes[i];
+    } else {
+      const double share = total > 0.0 ? work[i] / total : 1.0 / n;
+      const double g = std::ceil(ctx->prm.team_factor * share * nblocks);
+      b->team[i] = (int)std::max(1.0, std::min((double)nblocks, g));
+    }
+  }
+  b->order.resize(n);
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int a, int c) { return work[a] > work[c]; });
+  int rc = dev_alloc(ctx, (void**)&b->d_states, sizeof(SolveState) * n, &b->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&b->d_entries, sizeof(QueueEntry) * n, &b->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&b->d_ctl, sizeof(BatchCtl), &b->bytes);
+  if (rc != CVO_OK) return bail(rc);
+  if (cudaMallocHost((void**)&b->h_states, sizeof(SolveState) * n) != cudaSuccess)
+    return bail(fail(ctx, CVO_ERR_CUDA, "cudaMallocHost of batch states failed"));
+  std::memset(b->h_states, 0, sizeof(SolveState) * n);
+  std::vector<QueueEntry> ent(n);
+  long long slot = 0;
+  for (int q = 0; q < n; ++q) {
+    const int i = b->order[q];
+    ent[q].cfg = b->plans[i]->d_cfg;
+    ent[q].st = b->d_states + q;
+    ent[q].partials = b->plans[i]->d_partials;
+    ent[q].out = nullptr;
+    ent[q].team = b->team[i];
+    ent[q].slot0 = (int)slot;
+    slot += b->team[i];
+  }
+  BatchCtl ctl{};
+  ctl.q.tail = (unsigned long long)slot;
+  ctl.q.n_entries = (unsigned long long)n;
+  ctl.q.stop = 1;
+  CK(cudaMemcpyAsync(b->d_entries, ent.data(), sizeof(QueueEntry) * n, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(b->d_ctl, &ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // capture the launch once; a batch whose capture fails runs the same
+  // operations directly on the stream
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const cudaError_t e = record_batch_launch(b, ctx->stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess && g &&
+        cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+      b->graph = g;
+    } else {
+      if (g) cudaGraphDestroy(g);
+      b->exec = nullptr;
+    }
+    (void)cudaGetLastError();
+  }
+  *out = b;
+  return CVO_OK;
+}
+
+int cvo_batch_run(cvo_ctx* ctx, cvo_batch* b, const double* P0, double* P_out,
+                  cvo_stats* stats) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!b || std::find(ctx->batches.begin(), ctx->batches.end(), b) == ctx->batches.end())
+    return fail(ctx, CVO_ERR_NOT_FOUND, "unknown batch");
+  if (!P0 || !P_out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL pose array");
+  for (int i = 0; i < b->n; ++i) {
+    const int rc = check_pose(ctx, P0 + 16 * (size_t)i);
+    if (rc != CVO_OK) return rc;
+  }
+  CK(cudaSetDevice(ctx->device));
+  for (int q = 0; q < b->n; ++q) {
+    SolveState& hs = b->h_states[q];
+    std::memset(&hs, 0, sizeof(SolveState));
+    std::memcpy(hs.P0, P0 + 16 * (size_t)b->order[q], sizeof(double) * 16);
+  }
+  if (b->exec) {
+    CK(cudaGraphLaunch(b->exec, ctx->stream));
+  } else {
+    CK(record_batch_launch(b, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  int first = CVO_OK;
+  for (int q = 0; q < b->n; ++q) {
+    const int i = b->order[q];
+    const SolveState& hs = b->h_states[q];
+    std::memcpy(P_out + 16 * (size_t)i, hs.P, sizeof(double) * 16);
+    const int code = status_code(hs.status);
+    if (stats) {
+      fill_stats(&hs, &stats[i]);
+      stats[i].status = code;
+    }
+    if (code != CVO_OK && first == CVO_OK) first = code;
+  }
+  if (first != CVO_OK) fail(ctx, first, "a pair of the batch failed (see its stats)");
+  return first;
+}
+
+int cvo_batch_get_info(cvo_ctx* ctx, const cvo_batch* b, cvo_batch_info* info,
+                       int32_t* team_sizes) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!b || std::find(ctx->batches.begin(), ctx->batches.end(), b) == ctx->batches.end())
+    return fail(ctx, CVO_ERR_NOT_FOUND, "unknown batch");
+  if (info) {
+    info->pairs = b->n;
+    info->blocks = b->nblocks;
+    info->graph = b->exec ? 1 : 0;
+    info->max_team = *std::max_element(b->team.begin(), b->team.end());
+    size_t bytes = b->bytes;
+    for (const Plan* p : b->plans) bytes += p->bytes;
+    info->bytes = (int64_t)bytes;
+  }
+  if (team_sizes)
+    for (int i = 0; i < b->n; ++i) team_sizes[i] = b->team[i];
+  return CVO_OK;
+}
+
+int cvo_batch_destroy(cvo_ctx* ctx, cvo_batch* b) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!b || std::find(ctx->batches.begin(), ctx->batches.end(), b) == ctx->batches.end())
+    return fail(ctx, CVO_ERR_NOT_FOUND, "unknown batch");
+  destroy_batch(ctx, b);
+  return CVO_OK;
+}
 
 }  // extern "C"

@@ -27,6 +27,7 @@ constexpr int kMortonBits = 10;           // Morton quantisation per axis
 enum : int { kColorNone = 0, kColorKernel = 1, kColorDot = 2 };
 enum : int { kModeAlign = 0, kModeEval = 1 };
 enum : int { kStatusSegOverflow = 1, kStatusTimeout = 2 };   // bits of SolveState::status
+enum : int { kStatusIdleTimeout = 4 };   // queue kernel: a block gave up waiting for entries
 
 // One uniform-grid cell list over a target cloud (Sec. 5 sparsification:
 // only cells within the cutoff radius of a source point are visited).
@@ -105,6 +106,8 @@ struct SolveState {
   unsigned long long nnz_pass[2], cand_pass[2];
   unsigned long long nnz_eval, cand_eval;   // gradient pass of the last iteration
   unsigned int bar_count, bar_gen;          // grid barrier (zeroed before each launch)
+  unsigned int join_count, pad_join;        // queued solves: blocks of the team that have started
+  unsigned long long t_begin_ns, t_end_ns;  // global timer at the start and end of the solve
   double red_sums[10];                      // pass totals published by the barrier's last block
 };
 
@@ -116,6 +119,35 @@ struct IterRecord {
   float t_step_pass_ns, t_step_sync_ns;      //   block 0's own pass, and pass + barrier
   int replanned;
   long long grad_pairs, step_pairs, grad_candidates;
+};
+
+// Result of one queued solve as the host reads it (host-mapped memory for a
+// served request): written after the solve is published, `done` last.
+struct PairResult {
+  double P[16];
+  double F, t, ell;
+  double device_ms;
+  long long pair_evals, candidates;
+  int iters, converged, fallback_steps, no_ascent_steps, status;
+  int done;
+};
+
+// One pair of a queue. Entries are appended in slot order: entry e owns the
+// `team` slots starting at slot0 (the sum of the team sizes before it).
+struct QueueEntry {
+  const SolveCfg* cfg;
+  SolveState* st;            // zeroed, with P0 set, before the entry is published
+  double* partials;          // 2 * team * kPartialStride doubles
+  PairResult* out;           // NULL: the host reads st after the launch
+  int team, slot0;
+};
+
+// Queue control words (device memory for a batch, host-mapped for serving).
+// The host writes entries, then n_entries, then tail (release order).
+struct QueueCtl {
+  unsigned long long tail;       // published slots
+  unsigned long long n_entries;  // published entries
+  unsigned long long stop;       // nonzero: nothing more comes; blocks leave once all is claimed
 };
 
 // ---- grid.cu --------------------------------------------------------------
@@ -168,6 +200,13 @@ cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int 
 // kPartialStride doubles; records (may be NULL) one entry per iteration.
 cudaError_t launch_solve(int dp, int color_mode, int nblocks, const SolveCfg* cfg, SolveState* st,
                          double* partials, IterRecord* records, cudaStream_t s);
+// Many pairs in one cooperative launch of nblocks blocks (queue_kernel):
+// blocks claim slots through *head (zeroed before the launch) until the queue
+// is drained and ctl->stop is set, or until they have waited idle_limit_ns for
+// an entry (then *kstatus gets kStatusIdleTimeout).
+cudaError_t launch_queue(int dp, int color_mode, int nblocks, const QueueEntry* entries,
+                         const QueueCtl* ctl, unsigned long long* head, int* kstatus,
+                         unsigned long long idle_limit_ns, cudaStream_t s);
 // Co-resident blocks per SM of the solve kernel for this feature layout.
 int solve_blocks_per_sm(int dp, int color_mode);
 

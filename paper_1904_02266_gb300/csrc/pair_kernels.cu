@@ -49,6 +49,8 @@ namespace {
 constexpr float kFar = 1.0e18f;   // coordinate of padding points: never within any cutoff
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kSpinLimit = 1u << 22;   // barrier polls before giving up (~2 s)
+// a queued team waits for its last block to come free for at most this long
+constexpr unsigned long long kJoinLimitNs = 60ull * 1000 * 1000 * 1000;
 constexpr double kSkin = 0.10;              // plan radius margin (fraction of the cutoff)
 constexpr double kLoose = 1.25;             // replan when the plan radius exceeds this factor
 
@@ -89,8 +91,14 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// per-block iteration state (identical in every block)
+// per-block iteration state (identical in every block of a team)
 // ---------------------------------------------------------------------------
+
+// The blocks that solve one pair together: the whole grid for a single
+// solve, a contiguous run of claimed slots for a queued one.
+struct Team {
+  int rank, size;
+};
 
 struct BlockCtx {
   double P[16];           // current pose
@@ -377,14 +385,14 @@ __device__ void finish_step(const SolveCfg* cfg, BlockCtx& b, const double sums[
 // cooperative launch keeps all blocks resident. A block that polls for
 // kSpinLimit rounds raises kStatusTimeout and every block then leaves the
 // solve loop at its next barrier.
-__device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag) {
+__device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned g = gen;
     __threadfence();
     const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == (unsigned)nblk - 1) {
       atomicExch(&st->bar_count, 0u);
       __threadfence();
       atomicExch(&st->bar_gen, g + 1);
@@ -412,7 +420,7 @@ __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag) {
 // lane l adds blocks l, l + 32, ... (all loads issued first, then a pairwise
 // tree), then a shuffle tree across lanes. Results land in out[] (shared).
 // Must be called by every thread of the block.
-__device__ void reduce_partials(const double* partials, int nvals, double* out) {
+__device__ void reduce_partials(const double* partials, int nvals, double* out, int nblk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kMaxPerLane = 16;   // blocks per lane: up to 512 blocks
   for (int i = warp; i < nvals; i += kWarps) {
@@ -420,7 +428,7 @@ __device__ void reduce_partials(const double* partials, int nvals, double* out) 
 #pragma unroll
     for (int q = 0; q < kMaxPerLane; ++q) {
       const int b = lane + 32 * q;
-      v[q] = b < (int)gridDim.x ? __ldcg(&partials[(size_t)b * kPartialStride + i]) : 0.0;
+      v[q] = b < nblk ? __ldcg(&partials[(size_t)b * kPartialStride + i]) : 0.0;
     }
 #pragma unroll
     for (int w = kMaxPerLane / 2; w > 0; w >>= 1)
@@ -438,18 +446,18 @@ __device__ void reduce_partials(const double* partials, int nvals, double* out) 
 // gets the totals in sums[]. Bounded like grid_sync.
 template <class Smem>
 __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const double* partials,
-                                 int nvals) {
+                                 int nvals, int nblk) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-    sm.last = (arrived == gridDim.x - 1) ? 1 : 0;
+    sm.last = (arrived == (unsigned)nblk - 1) ? 1 : 0;
   }
   __syncthreads();
   int ok = 1;
   const unsigned g = gen;
   if (sm.last) {
-    reduce_partials(partials, nvals, sm.sums);
+    reduce_partials(partials, nvals, sm.sums, nblk);
     if (threadIdx.x < (unsigned)nvals) st->red_sums[threadIdx.x] = sm.sums[threadIdx.x];
     __threadfence();
     __syncthreads();
@@ -479,6 +487,36 @@ __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const 
   if (threadIdx.x == 0) {
     if (sm.last) sm.flag = 1;
     if (ld_acquire((const unsigned*)&st->status) & kStatusTimeout) sm.flag = 0;
+  }
+  __syncthreads();
+  return sm.flag != 0;
+}
+
+// Start of a queued solve: wait until every block of the team has claimed its
+// slot. Blocks of a team come free at different times (each finishes the pair
+// it held), so this wait can last as long as one pair's solve; it is bounded
+// by kJoinLimitNs of the global timer, after which the pair fails with
+// kStatusTimeout.
+template <class Smem>
+__device__ bool team_join(SolveState* st, int team_size, Smem& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(&st->join_count, 1u);
+    const unsigned long long t_start = globaltimer();
+    unsigned polls = 0;
+    while (ld_acquire(&st->join_count) < (unsigned)team_size) {
+      if ((++polls & 255u) == 0 && globaltimer() - t_start > kJoinLimitNs) {
+        ok = 0;
+        atomicOr(&st->status, (int)kStatusTimeout);
+        break;
+      }
+      __nanosleep(256);
+    }
+    __threadfence();
+    if (ld_acquire((const unsigned*)&st->status) & kStatusTimeout) ok = 0;
+    sm.flag = ok;
   }
   __syncthreads();
   return sm.flag != 0;
@@ -598,6 +636,8 @@ struct SolveSmem {
   int bnd_group[2 * kWarps];
   double sums[10];
   int flag, last;
+  long long q_slot;                 // queue: claimed slot (-1: none left)
+  int q_entry;                      //        entry that slot belongs to
   BlockCtx b;
 };
 
@@ -633,7 +673,7 @@ __device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, lo
 // Place the block's warps on an even split of the plan's work: warp w owns the
 // chunks whose work starts in [floor(w TW/NW), floor((w+1) TW/NW)).
 template <int DPS, int NU>
-__device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid) {
+__device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid, Team team) {
   const ClusterView& cv = cfg->clusters[sm.b.level];
   const int ng = (cv.ncl + 31) / 32;
   const int per = (ng + kThreads - 1) / kThreads;
@@ -650,13 +690,13 @@ __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid)
     __syncthreads();
   }
   const long long TW = sm.scan[kThreads - 1];
-  const long long NW = (long long)gridDim.x * kWarps;
+  const long long NW = (long long)team.size * kWarps;
   long long run = sm.scan[tid] - local;
   for (int gi = g0; gi < g1; ++gi) {
     const long long gtests = __ldcg(&cfg->group_agg[gi]);
 #pragma unroll
     for (int q = 0; q < 2 * kWarps; ++q) {
-      const long long w = (long long)blockIdx.x * kWarps + (q >> 1) + (q & 1);
+      const long long w = (long long)team.rank * kWarps + (q >> 1) + (q & 1);
       const long long s = TW > 0 ? (w * TW) / NW : 0;
       if (gtests > 0 && s >= run && s < run + gtests) {
         sm.bnd_group[q] = gi;
@@ -670,7 +710,7 @@ __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid)
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int q = 2 * warp + h;
-    const long long w = (long long)blockIdx.x * kWarps + warp + h;
+    const long long w = (long long)team.rank * kWarps + warp + h;
     const long long s = TW > 0 ? (w * TW) / NW : 0;
     int c, jj;
     if (TW == 0 || s >= TW || sm.bnd_group[q] < 0) {
@@ -896,7 +936,7 @@ __device__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
 
 // One pass over the block's warps, then the block partial (fixed order).
 template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials) {
+__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials, int rank) {
   constexpr int NACC = STEP ? 5 : 7;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float acc[7];
@@ -932,7 +972,7 @@ __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* pa
       for (int w = 0; w < kWarps; ++w) n += __float_as_uint(sm.red[w][lane]);
       s = (double)n;
     }
-    partials[(size_t)blockIdx.x * kPartialStride + lane] = s;
+    partials[(size_t)rank * kPartialStride + lane] = s;
   }
 }
 
@@ -956,20 +996,17 @@ __device__ void publish(SolveState* st, const BlockCtx& b) {
   st->cand_eval = b.cand_grad;
 }
 
-// The whole solve (or one evaluation) in one cooperative launch.
-template <int DP, int MODE>
-__global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
-solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
-             double* __restrict__ partials, IterRecord* __restrict__ records) {
-  constexpr int DPS = DP > 0 ? DP : 1;
-  constexpr int NU = 4;
-  __shared__ SolveSmem<DPS, NU> sm;
+// The whole solve of one pair (or one evaluation) by one team of blocks.
+template <int DP, int MODE, int DPS, int NU>
+__device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
+                           double* __restrict__ partials, IterRecord* __restrict__ records,
+                           Team team, SolveSmem<DPS, NU>& sm, bool join) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned gen = 0;
   double* part_g = partials;
-  double* part_s = partials + (size_t)gridDim.x * kPartialStride;
-  const long long NW = (long long)gridDim.x * kWarps;
-  const long long gw = (long long)blockIdx.x * kWarps + warp;
+  double* part_s = partials + (size_t)team.size * kPartialStride;
+  const long long NW = (long long)team.size * kWarps;
+  const long long gw = (long long)team.rank * kWarps + warp;
 
   if (tid == 0) {
     BlockCtx& b = sm.b;
@@ -990,16 +1027,21 @@ solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
     if (!b.done) begin_iteration(cfg, b);
   }
   __syncthreads();
+  if (join && !team_join(st, team.size, sm)) {
+    if (tid == 0) sm.b.done = 1;   // a team that never assembled runs no iteration
+    __syncthreads();
+  }
+  if (team.rank == 0 && tid == 0) st->t_begin_ns = globaltimer();
 
   while (!sm.b.done) {
     unsigned long long t0 = 0, t1 = 0, t2 = 0, tg1 = 0, tg2 = 0, ts1 = 0, ts2 = 0;
-    const bool stamp = records != nullptr && blockIdx.x == 0 && tid == 0;
+    const bool stamp = records != nullptr && team.rank == 0 && tid == 0;
     if (stamp) t0 = globaltimer();
     const int replan = sm.b.need_plan;
     if (replan) {
       const ClusterView& cv = cfg->clusters[sm.b.level];
       for (long long c = gw; c < cv.ncl; c += NW) plan_cluster(cfg, sm.b, st, (int)c, lane);
-      if (!grid_sync(st, gen, &sm.flag)) break;
+      if (!grid_sync(st, gen, &sm.flag, team.size)) break;
       const int ng = (cv.ncl + 31) / 32;
       for (long long gi = gw; gi < ng; gi += NW) {
         const int c = (int)gi * 32 + lane;
@@ -1009,24 +1051,24 @@ solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
         for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(kFull, w, off);
         if (lane == 0) cfg->group_agg[gi] = w;
       }
-      if (!grid_sync(st, gen, &sm.flag)) break;
-      split_work<DPS, NU>(cfg, sm, tid);
+      if (!grid_sync(st, gen, &sm.flag, team.size)) break;
+      split_work<DPS, NU>(cfg, sm, tid, team);
       if (tid == 0) sm.b.need_plan = 0;
       __syncthreads();
     }
     if (stamp) t1 = globaltimer();
     // ---- gradient pass ----
-    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g);
+    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g, team.rank);
     if (stamp) tg1 = globaltimer();
-    if (!grid_sync_reduce(st, gen, sm, part_g, 9)) break;
+    if (!grid_sync_reduce(st, gen, sm, part_g, 9, team.size)) break;
     if (stamp) tg2 = globaltimer();
     if (tid == 0) finish_gradient(cfg, sm.b, sm.sums);
     __syncthreads();
     if (stamp) t2 = globaltimer();
     // ---- step pass ----
-    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s);
+    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s, team.rank);
     if (stamp) ts1 = globaltimer();
-    if (!grid_sync_reduce(st, gen, sm, part_s, 7)) break;
+    if (!grid_sync_reduce(st, gen, sm, part_s, 7, team.size)) break;
     if (stamp) ts2 = globaltimer();
     {
       if (tid == 0) {
@@ -1054,7 +1096,144 @@ solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0 && tid == 0) publish(st, sm.b);
+  if (team.rank == 0 && tid == 0) {
+    publish(st, sm.b);
+    st->t_end_ns = globaltimer();
+  }
+  __syncthreads();
+}
+
+// The whole solve (or one evaluation) in one cooperative launch: the grid is
+// one team.
+template <int DP, int MODE>
+__global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
+solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
+             double* __restrict__ partials, IterRecord* __restrict__ records) {
+  constexpr int DPS = DP > 0 ? DP : 1;
+  constexpr int NU = 4;
+  __shared__ SolveSmem<DPS, NU> sm;
+  solve_pair<DP, MODE, DPS, NU>(cfg, st, partials, records, Team{(int)blockIdx.x, (int)gridDim.x},
+                                sm, false);
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_sys_u64(const void* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_sys_s32(int* p, int v) {
+  asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Entry fields read at system scope: the entries of a served queue live in
+// host memory that the host appends to while the kernel runs.
+__device__ QueueEntry load_entry(const QueueEntry* e) {
+  static_assert(sizeof(QueueEntry) == 40, "QueueEntry layout");
+  QueueEntry r;
+  unsigned long long w[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) w[i] = ld_relaxed_sys_u64(reinterpret_cast<const unsigned long long*>(e) + i);
+  memcpy(&r, w, sizeof(r));
+  return r;
+}
+
+// Claim the next slot (thread 0): slots are handed out in order, so every
+// slot of an entry is claimed before any slot of a later one. A team whose
+// first blocks start before the rest have claimed their slots waits at its
+// first barrier; the entries ahead of it never wait on later ones, so the
+// blocks they hold come free in bounded time and staff it.
+__device__ void claim_slot(const QueueEntry* entries, const QueueCtl* ctl,
+                           unsigned long long* head, int* kstatus,
+                           unsigned long long idle_limit_ns, long long* slot_out,
+                           int* entry_out) {
+  const unsigned long long t_start = globaltimer();
+  unsigned polls = 0;
+  for (;;) {
+    const unsigned long long tail = ld_acquire_sys_u64(&ctl->tail);
+    const unsigned long long h = atomicAdd(head, 0ull);
+    if (h < tail) {
+      if (atomicCAS(head, h, h + 1) != h) continue;
+      // the entry holding slot h: the last one whose first slot is <= h
+      const unsigned long long ne = ld_relaxed_sys_u64(&ctl->n_entries);
+      long long lo = 0, hi = (long long)ne;   // invariant: entry lo starts at or before h
+      while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        const QueueEntry em = load_entry(entries + mid);
+        if ((unsigned long long)em.slot0 <= h) lo = mid;
+        else hi = mid;
+      }
+      *slot_out = (long long)h;
+      *entry_out = (int)lo;
+      return;
+    }
+    if (ld_acquire_sys_u64(&ctl->stop) != 0) break;
+    if ((++polls & 63u) == 0 && globaltimer() - t_start > idle_limit_ns) {
+      atomicOr(kstatus, (int)kStatusIdleTimeout);
+      break;
+    }
+    __nanosleep(1024);
+  }
+  *slot_out = -1;
+  *entry_out = -1;
+}
+
+// Solve results for the host: written by the team's first block once the
+// solve is published, the done flag last (release at system scope).
+__device__ void write_result(const SolveState* st, PairResult* out) {
+  for (int i = 0; i < 16; ++i) out->P[i] = st->P[i];
+  out->F = st->F;
+  out->t = st->t;
+  out->ell = st->ell;
+  out->device_ms = (double)(st->t_end_ns - st->t_begin_ns) * 1e-6;
+  out->pair_evals = (long long)st->nnz_total;
+  out->candidates = (long long)st->cand_total;
+  out->iters = st->iter;
+  out->converged = st->converged;
+  out->fallback_steps = st->fallback_steps;
+  out->no_ascent_steps = st->no_ascent_steps;
+  out->status = st->status;
+  __threadfence_system();
+  st_release_sys_s32(&out->done, 1);
+}
+
+// Many pairs in one persistent cooperative launch. Blocks claim slots of a
+// queue of entries; the blocks holding the slots of one entry form its team.
+template <int DP, int MODE>
+__global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
+queue_kernel(const QueueEntry* __restrict__ entries, const QueueCtl* __restrict__ ctl,
+             unsigned long long* __restrict__ head, int* __restrict__ kstatus,
+             unsigned long long idle_limit_ns) {
+  constexpr int DPS = DP > 0 ? DP : 1;
+  constexpr int NU = 4;
+  __shared__ SolveSmem<DPS, NU> sm;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long long slot;
+      int e;
+      claim_slot(entries, ctl, head, kstatus, idle_limit_ns, &slot, &e);
+      sm.q_slot = slot;
+      sm.q_entry = e;
+    }
+    __syncthreads();
+    if (sm.q_slot < 0) break;
+    const QueueEntry en = load_entry(entries + sm.q_entry);
+    const Team team{(int)(sm.q_slot - en.slot0), en.team};
+    solve_pair<DP, MODE, DPS, NU>(en.cfg, en.st, en.partials, nullptr, team, sm, true);
+    if (team.rank == 0 && threadIdx.x == 0) {
+      if (en.out) {
+        __threadfence();
+        write_result(en.st, en.out);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 template <int DP, int MODE>
@@ -1062,6 +1241,15 @@ cudaError_t launch_solve_t(int nblocks, const SolveCfg* cfg, SolveState* st, dou
                            IterRecord* records, cudaStream_t s) {
   void* args[] = {(void*)&cfg, (void*)&st, (void*)&partials, (void*)&records};
   return cudaLaunchCooperativeKernel((const void*)solve_kernel<DP, MODE>, dim3(nblocks),
+                                     dim3(kThreads), args, 0, s);
+}
+
+template <int DP, int MODE>
+cudaError_t launch_queue_t(int nblocks, const QueueEntry* entries, const QueueCtl* ctl,
+                           unsigned long long* head, int* kstatus, unsigned long long idle_ns,
+                           cudaStream_t s) {
+  void* args[] = {(void*)&entries, (void*)&ctl, (void*)&head, (void*)&kstatus, (void*)&idle_ns};
+  return cudaLaunchCooperativeKernel((const void*)queue_kernel<DP, MODE>, dim3(nblocks),
                                      dim3(kThreads), args, 0, s);
 }
 
@@ -1088,6 +1276,25 @@ cudaError_t launch_solve(int dp, int color_mode, int nblocks, const SolveCfg* cf
   if (dp == 3) return launch_solve_t<3, kColorDot>(nblocks, cfg, st, partials, records, s);
   if (dp == 5) return launch_solve_t<5, kColorDot>(nblocks, cfg, st, partials, records, s);
   return launch_solve_t<8, kColorDot>(nblocks, cfg, st, partials, records, s);
+}
+
+cudaError_t launch_queue(int dp, int color_mode, int nblocks, const QueueEntry* entries,
+                         const QueueCtl* ctl, unsigned long long* head, int* kstatus,
+                         unsigned long long idle_limit_ns, cudaStream_t s) {
+  if (color_mode == kColorNone || dp == 0)
+    return launch_queue_t<0, kColorNone>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+  if (color_mode == kColorKernel) {
+    if (dp == 3)
+      return launch_queue_t<3, kColorKernel>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+    if (dp == 5)
+      return launch_queue_t<5, kColorKernel>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+    return launch_queue_t<8, kColorKernel>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+  }
+  if (dp == 3)
+    return launch_queue_t<3, kColorDot>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+  if (dp == 5)
+    return launch_queue_t<5, kColorDot>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+  return launch_queue_t<8, kColorDot>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
 }
 
 int solve_blocks_per_sm(int dp, int color_mode) {

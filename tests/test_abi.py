@@ -62,19 +62,30 @@ def test_host_only_calls(lib_path):
 
 
 def test_struct_layouts_match_the_header(lib_path):
-    """ctypes mirrors of the ABI structs have the C sizes (checked by
-    compiling a tiny C program against the header)."""
+    """ctypes mirrors of the ABI structs have the C sizes and field offsets
+    (checked by compiling a tiny C program against the header)."""
     import paper_1904_02266_gb300 as cvo
-    src = ('#include <stdio.h>\n#include "cvo.h"\nint main(void){printf("%zu %zu %zu %zu\\n",'
-           'sizeof(cvo_params),sizeof(cvo_eval_result),sizeof(cvo_stats),'
-           'sizeof(cvo_iter_profile));return 0;}\n')
+    structs = [cvo.cvo_params, cvo.cvo_eval_result, cvo.cvo_stats, cvo.cvo_iter_profile,
+               cvo.cvo_batch_info]
+    lines = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("%zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({name}, {f}));')
+    src = ('#include <stdio.h>\n#include <stddef.h>\n#include "cvo.h"\nint main(void){'
+           + "".join(lines) + 'return 0;}\n')
     tmp = os.path.join(ROOT, "paper_1904_02266_gb300", "_build")
+    os.makedirs(tmp, exist_ok=True)
     c = os.path.join(tmp, "abi_sizes.c")
     exe = os.path.join(tmp, "abi_sizes")
     with open(c, "w") as fh:
         fh.write(src)
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, c], check=True)
-    sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
-                                            check=True).stdout.split()]
-    assert sizes == [ctypes.sizeof(cvo.cvo_params), ctypes.sizeof(cvo.cvo_eval_result),
-                     ctypes.sizeof(cvo.cvo_stats), ctypes.sizeof(cvo.cvo_iter_profile)]
+    got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = []
+    for st in structs:
+        want.append(ctypes.sizeof(st))
+        want.extend(getattr(st, f).offset for f, _ in st._fields_)
+    assert got == want

@@ -1,0 +1,135 @@
+"""Batches: many uneven pairs solved in one persistent launch (cvo_batch_*),
+called through the C ABI.
+
+Each pair of a batch runs the same iteration as a single cvo_align; only the
+team of blocks that solves it (and so the order of the FP64 sums over
+blocks) differs. So every pair is held to the oracle's pose tolerance
+(1e-4 rad, 1e-4 m), pairs that share clouds, team size and start pose must
+agree bit for bit, and a replay of the captured graph must reproduce the
+previous run exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+POSE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def cvo():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1904_02266_gb300 as m
+    return m
+
+
+def _oracle_params(ctx_params, ell0):
+    p = oracle.Params()
+    for k in ("ell_decay", "ell_min", "sigma", "kcut", "ell_color", "color_scale", "a2", "b2",
+              "max_iters", "eps_pose", "eps_grad", "step_order"):
+        setattr(p, k, getattr(ctx_params, k))
+    p.ell0 = ell0
+    return p
+
+
+@pytest.fixture(scope="module")
+def uneven():
+    # sizes spread over a factor of ten, each pair with its own motion and ell0
+    return synth.batch_pairs(n_pairs=10, seed=synth.seed_for(3, 1), n_range=(400, 4000))
+
+
+def test_batch_matches_single_solves(cvo, uneven):
+    with cvo.Context(device=0) as ctx:
+        hs = [(ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])) for d in uneven]
+        ell0 = [d["ell0"] for d in uneven]
+        P0 = np.stack([np.eye(4)] * len(uneven))
+        with ctx.batch([t for t, _ in hs], [s for _, s in hs], ell0=ell0) as b:
+            info = b.info()
+            assert info["pairs"] == len(uneven) and info["graph"] == 1
+            teams = info["teams"]
+            assert teams.min() >= 1 and teams.max() <= info["blocks"]
+            # the largest pair gets at least as many blocks as the smallest
+            sizes = [len(d["X"]) * len(d["Z"]) for d in uneven]
+            assert teams[int(np.argmax(sizes))] >= teams[int(np.argmin(sizes))]
+            P, stats = b.run(P0)
+            P2, _ = b.run(P0)
+        assert np.array_equal(P, P2), "graph replay changed a result"
+        for i, d in enumerate(uneven):
+            assert stats[i]["status"] == 0
+            ctx2 = cvo.Context(device=0, ell0=ell0[i])
+            try:
+                t, s = ctx2.set_cloud(d["X"], d["FX"]), ctx2.set_cloud(d["Z"], d["FZ"])
+                Ps, sts = ctx2.align(t, s)
+            finally:
+                ctx2.close()
+            ang, tr = oracle.pose_error(P[i], Ps)
+            assert ang < POSE_TOL and tr < POSE_TOL, (i, ang, tr)
+            assert abs(stats[i]["iters"] - sts["iters"]) <= 2, (i, stats[i]["iters"], sts["iters"])
+            # and the truth is recovered to the noise level
+            ang_gt, tr_gt = oracle.pose_error(P[i], d["P_gt"])
+            assert ang_gt < 0.02 and tr_gt < 0.02, (i, ang_gt, tr_gt)
+
+
+def test_batch_matches_oracle(cvo):
+    pairs = synth.batch_pairs(n_pairs=3, seed=synth.seed_for(3, 2), n_range=(500, 1200))
+    with cvo.Context(device=0) as ctx:
+        hs = [(ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])) for d in pairs]
+        with ctx.batch([t for t, _ in hs], [s for _, s in hs],
+                       ell0=[d["ell0"] for d in pairs]) as b:
+            P, stats = b.run(np.stack([np.eye(4)] * len(pairs)))
+        for i, d in enumerate(pairs):
+            res = oracle.align(d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4),
+                               _oracle_params(ctx.params, d["ell0"]))
+            ang, tr = oracle.pose_error(P[i], res["P"])
+            assert ang < POSE_TOL and tr < POSE_TOL, (i, ang, tr)
+            assert stats[i]["iters"] == res["iters"], (i, stats[i]["iters"], res["iters"])
+
+
+def test_batch_duplicates_and_fixed_teams(cvo, uneven):
+    d0, d1 = uneven[0], uneven[3]
+    with cvo.Context(device=0) as ctx:
+        a = (ctx.set_cloud(d0["X"], d0["FX"]), ctx.set_cloud(d0["Z"], d0["FZ"]))
+        c = (ctx.set_cloud(d1["X"], d1["FX"]), ctx.set_cloud(d1["Z"], d1["FZ"]))
+        # the same pair three times with one team size, plus another pair
+        tg = [a[0], c[0], a[0], a[0]]
+        sr = [a[1], c[1], a[1], a[1]]
+        teams = [7, 3, 7, 7]
+        with ctx.batch(tg, sr, team_sizes=teams) as b:
+            assert list(b.info()["teams"]) == teams
+            P, stats = b.run(np.stack([np.eye(4)] * 4))
+        assert np.array_equal(P[0], P[2]) and np.array_equal(P[0], P[3])
+        assert stats[0]["pair_evals"] == stats[2]["pair_evals"]
+        # one block per pair versus the whole grid on the same pair
+        with ctx.batch([a[0]], [a[1]], team_sizes=[1]) as b1:
+            P1, _ = b1.run(np.eye(4)[None])
+        Pa, _ = ctx.align(a[0], a[1])
+        ang, tr = oracle.pose_error(P1[0], Pa)
+        assert ang < POSE_TOL and tr < POSE_TOL
+
+
+def test_batch_errors_and_busy_clouds(cvo, uneven):
+    d = uneven[1]
+    with cvo.Context(device=0) as ctx:
+        t, s = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+        with pytest.raises(cvo.CvoError) as e:
+            ctx.batch([t], [s], team_sizes=[0])
+        assert e.value.code == cvo.CVO_ERR_INVALID_ARG
+        with pytest.raises(cvo.CvoError) as e:
+            ctx.batch([t], [s + 17])
+        assert e.value.code == cvo.CVO_ERR_NOT_FOUND
+        with pytest.raises(cvo.CvoError) as e:
+            ctx.batch([t], [s], ell0=[-1.0])
+        assert e.value.code == cvo.CVO_ERR_INVALID_ARG
+        b = ctx.batch([t], [s])
+        with pytest.raises(cvo.CvoError) as e:
+            ctx.release(s)
+        assert e.value.code == cvo.CVO_ERR_BUSY
+        with pytest.raises(cvo.CvoError) as e:
+            b.run(np.full((1, 4, 4), np.nan))
+        assert e.value.code == cvo.CVO_ERR_INVALID_ARG
+        b.close()
+        ctx.release(s)   # free again once the batch is gone
