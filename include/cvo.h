@@ -238,6 +238,71 @@ int cvo_batch_get_info(cvo_ctx* ctx, const cvo_batch* batch, cvo_batch_info* inf
 /* Free the batch's plans, states and graph. */
 int cvo_batch_destroy(cvo_ctx* ctx, cvo_batch* batch);
 
+/* ---- request loop: continuous batching of frame-pair solves -------------- */
+
+/* One request: align a new frame (the source) to a resident keyframe (the
+ * target). The frame arrays are copied before cvo_submit returns. */
+typedef struct {
+    int32_t target;        /* keyframe handle (cvo_set_cloud); kept resident with its cell lists */
+    const float* xyz;      /* frame points, n x 3 host float32 */
+    const float* feat;     /* frame features, n x feat_dim host float32 (may be NULL when
+                              feat_dim == 0 or color_mode is NONE) */
+    int64_t n;             /* 1 <= n <= 2^22 */
+    double P0[16];         /* initial pose, row-major, mapping the frame into the keyframe */
+    double ell0;           /* initial lengthscale; 0 = the context's */
+} cvo_request;
+
+/* Outcome of one request (cvo_poll). */
+typedef struct {
+    double P[16];          /* final pose */
+    cvo_stats stats;       /* solve statistics; stats.status is the request's status */
+    double queue_ms;       /* cvo_submit until the request was admitted (memory reserved) */
+    double latency_ms;     /* cvo_submit until the result was ready */
+} cvo_result;
+
+typedef struct {
+    int reserve_blocks;    /* block slots of the solve kernel's full occupancy that the
+                              serving kernel leaves free, so that the kernels preparing new
+                              frames can run while solves do; >= 1; 8 */
+    int max_inflight;      /* requests admitted to the device at once, in [1, 65536]; 1024 */
+    double linger_ms;      /* the serving kernel stays resident this long without work; 0.5 */
+} cvo_serve_params;
+
+/* Fill *p with the defaults listed in cvo_serve_params. */
+void cvo_serve_params_default(cvo_serve_params* p);
+
+/* Start the context's request loop (cvo_submit starts it with the defaults
+ * when it is not running). A host thread admits queued requests in arrival
+ * order while the context's HBM budget allows (a request that could never
+ * fit fails with CVO_ERR_OUT_OF_BUDGET; one that fits only after others
+ * finish waits), uploads and prepares each frame on the context stream, and
+ * hands it to one persistent cooperative kernel that stays resident while
+ * there is work: its blocks claim each request's team of slots as they come
+ * free, so requests that arrive while others are on the GPU start as soon as
+ * blocks and memory allow, and their solves overlap. A request's team size is
+ * about team_factor * (its share of the estimated work in the system) of the
+ * kernel's blocks. Each solve runs the same iteration as cvo_align. While the
+ * loop runs, cvo_align, cvo_align_profile, cvo_eval and cvo_batch_run return
+ * CVO_ERR_BUSY (their kernels need the whole GPU resident). Errors:
+ * CVO_ERR_BUSY if the loop already runs, CVO_ERR_INVALID_ARG for bad params. */
+int cvo_serve_start(cvo_ctx* ctx, const cvo_serve_params* params);
+
+/* Queue a request; *ticket identifies it for cvo_poll. The keyframe cannot be
+ * released (CVO_ERR_BUSY) until every request naming it has been polled
+ * complete. Errors: CVO_ERR_INVALID_ARG (NULL or bad fields, non-finite
+ * pose), CVO_ERR_NOT_FOUND (unknown keyframe). */
+int cvo_submit(cvo_ctx* ctx, const cvo_request* req, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 and *out filled (and the ticket retired) when the
+ * request has finished, *done = 0 otherwise. The request's own outcome is
+ * out->stats.status (CVO_OK, CVO_ERR_OUT_OF_BUDGET, CVO_ERR_TIMEOUT, ...).
+ * CVO_ERR_NOT_FOUND for an unknown or already retired ticket. */
+int cvo_poll(cvo_ctx* ctx, uint64_t ticket, cvo_result* out, int* done);
+
+/* Finish every queued and running request, then stop the loop and free its
+ * device resources. Results stay available to cvo_poll. */
+int cvo_serve_stop(cvo_ctx* ctx);
+
 /* Gradient pass for callers that must not allocate device memory during the
  * call: a program whose device memory is all owned by its own pool or fixed
  * at start-up (a real-time loop with a frozen footprint, an embedding host

@@ -39,6 +39,8 @@ CVO_MAX_FEAT = 8
 EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
            "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile", "cvo_stream",
            "cvo_batch_create", "cvo_batch_run", "cvo_batch_get_info", "cvo_batch_destroy",
+           "cvo_serve_params_default", "cvo_serve_start", "cvo_submit", "cvo_poll",
+           "cvo_serve_stop",
            "cvo_eval_gradient_static", "cvo_strerror", "cvo_last_error")
 
 
@@ -96,6 +98,21 @@ class cvo_batch_info(ctypes.Structure):
                 ("max_team", ctypes.c_int), ("bytes", ctypes.c_int64)]
 
 
+class cvo_request(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_int32), ("xyz", ctypes.c_void_p), ("feat", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("P0", ctypes.c_double * 16), ("ell0", ctypes.c_double)]
+
+
+class cvo_result(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_double * 16), ("stats", cvo_stats), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+class cvo_serve_params(ctypes.Structure):
+    _fields_ = [("reserve_blocks", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("linger_ms", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -141,6 +158,13 @@ def load_library(path: str = LIB_PATH):
         lib.cvo_batch_run.argtypes = [vp, vp, dp, dp, ctypes.POINTER(cvo_stats)]
         lib.cvo_batch_get_info.argtypes = [vp, vp, ctypes.POINTER(cvo_batch_info), i32p]
         lib.cvo_batch_destroy.argtypes = [vp, vp]
+        lib.cvo_serve_params_default.argtypes = [ctypes.POINTER(cvo_serve_params)]
+        lib.cvo_serve_params_default.restype = None
+        lib.cvo_serve_start.argtypes = [vp, ctypes.POINTER(cvo_serve_params)]
+        lib.cvo_submit.argtypes = [vp, ctypes.POINTER(cvo_request), ctypes.POINTER(ctypes.c_uint64)]
+        lib.cvo_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(cvo_result),
+                                 ctypes.POINTER(ctypes.c_int)]
+        lib.cvo_serve_stop.argtypes = [vp]
         lib.cvo_stream.argtypes = [vp]
         lib.cvo_stream.restype = ctypes.c_void_p
         lib.cvo_strerror.argtypes = [ctypes.c_int]
@@ -149,7 +173,8 @@ def load_library(path: str = LIB_PATH):
         lib.cvo_last_error.restype = ctypes.c_char_p
         for name in ("cvo_create", "cvo_destroy", "cvo_set_cloud", "cvo_release_cloud",
                      "cvo_eval", "cvo_align", "cvo_batch_create", "cvo_batch_run",
-                     "cvo_batch_get_info", "cvo_batch_destroy"):
+                     "cvo_batch_get_info", "cvo_batch_destroy", "cvo_serve_start",
+                     "cvo_submit", "cvo_poll", "cvo_serve_stop"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -317,6 +342,49 @@ def cvo_batch_destroy(ctx, batch) -> None:
     _check(ctx, load_library().cvo_batch_destroy(ctx, batch))
 
 
+def cvo_serve_params_default() -> cvo_serve_params:
+    p = cvo_serve_params()
+    load_library().cvo_serve_params_default(ctypes.byref(p))
+    return p
+
+
+def cvo_serve_start(ctx, params: cvo_serve_params | None = None) -> None:
+    _check(ctx, load_library().cvo_serve_start(
+        ctx, ctypes.byref(params) if params is not None else None))
+
+
+def cvo_submit(ctx, target: int, xyz, feat=None, P0=None, ell0: float = 0.0) -> int:
+    """Queue the alignment of a frame (host arrays, copied) to a resident
+    keyframe; returns the ticket."""
+    x = np.ascontiguousarray(xyz, dtype=np.float32)
+    f = None if feat is None else np.ascontiguousarray(feat, dtype=np.float32)
+    r = cvo_request()
+    r.target = int(target)
+    r.xyz = x.ctypes.data
+    r.feat = None if f is None else f.ctypes.data
+    r.n = int(x.shape[0])
+    r.P0[:] = np.asarray(np.eye(4) if P0 is None else P0, dtype=np.float64).reshape(16)
+    r.ell0 = float(ell0)
+    t = ctypes.c_uint64(0)
+    _check(ctx, load_library().cvo_submit(ctx, ctypes.byref(r), ctypes.byref(t)))
+    return int(t.value)
+
+
+def cvo_poll(ctx, ticket: int):
+    """None while the request runs; else (pose, stats dict, queue_ms, latency_ms)."""
+    out = cvo_result()
+    done = ctypes.c_int(0)
+    _check(ctx, load_library().cvo_poll(ctx, int(ticket), ctypes.byref(out), ctypes.byref(done)))
+    if not done.value:
+        return None
+    stats = {k: getattr(out.stats, k) for k, _ in cvo_stats._fields_}
+    return np.array(out.P[:]).reshape(4, 4), stats, out.queue_ms, out.latency_ms
+
+
+def cvo_serve_stop(ctx) -> None:
+    _check(ctx, load_library().cvo_serve_stop(ctx))
+
+
 def cvo_eval_gradient_static(x, fx, z, fz, params: cvo_params, P, ell: float, out,
                              stream=None) -> None:
     """Allocation-free gradient pass on device tensors (torch CUDA float32, or
@@ -410,6 +478,21 @@ class Context:
 
     def batch(self, targets, sources, ell0=None, team_sizes=None) -> "Batch":
         return Batch(self, targets, sources, ell0, team_sizes)
+
+    def serve_start(self, **params) -> None:
+        p = cvo_serve_params_default()
+        for k, v in params.items():
+            setattr(p, k, v)
+        cvo_serve_start(self.ctx, p)
+
+    def submit(self, target: int, xyz, feat=None, P0=None, ell0: float = 0.0) -> int:
+        return cvo_submit(self.ctx, target, xyz, feat, P0, ell0)
+
+    def poll(self, ticket: int):
+        return cvo_poll(self.ctx, ticket)
+
+    def serve_stop(self) -> None:
+        cvo_serve_stop(self.ctx)
 
     @property
     def stream(self) -> int:

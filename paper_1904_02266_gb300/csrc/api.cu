@@ -18,140 +18,35 @@
 
 #include "../../include/cvo.h"
 #include "cvo_internal.cuh"
+#include "runtime.h"
 
 using namespace cvo;
 
 const char* cvo_static_last_error();   // noalloc.cu
 
-namespace {
-
-struct Grid {
-  double h_req = 0.0;   // requested cell edge (cache key)
-  GridView view{};
-  float4* xyz = nullptr;
-  float* feat = nullptr;
-  int* cell_start = nullptr;
-  size_t bytes = 0;
-};
-
-struct Clusters {
-  float max_edge = 0.f;  // cache key
-  int* cstart = nullptr;
-  int ncl = 0;
-  size_t bytes = 0;
-};
-
-struct Cloud {
-  int64_t n = 0;
-  int n_pad = 0;
-  int D = 0, dp = 0;
-  double c[3] = {0, 0, 0};
-  float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // bounding box, centred frame
-  MortonFrame mf{};
-  float4* xyz = nullptr;  // packed, original order
-  float* feat = nullptr;
-  float4* zs = nullptr;   // Morton order (source role, and input of the cell lists)
-  float* zf = nullptr;
-  double radius = 0.0;    // max |x'| over the centred cloud (from its bounding box)
-  std::vector<Grid> grids;
-  std::vector<Clusters> clusters;
-  size_t bytes = 0;
-  int refs = 0;           // batches that use the cloud
-};
-
-struct Plan {
-  int tgt = -1, src = -1;
-  SolveCfg h_cfg{};
-  SolveCfg* d_cfg = nullptr;
-  IterConst* d_iters = nullptr;
-  SolveState* d_state = nullptr;
-  double* d_partials = nullptr;
-  IterRecord* d_records = nullptr;
-  int* seg_xs = nullptr;
-  int* seg_pref = nullptr;
-  int* cl_nseg = nullptr;
-  int* cl_cand = nullptr;
-  long long* group_agg = nullptr;
-  int cap_iters = 0, cap_ncl = 0;
-  int nblocks = 0;
-  int n_iters = 0;
-  int dp = 0, color_mode = 0;
-  size_t bytes = 0;
-};
-
-// Queue control of a batch launch (device memory): the control words, the
-// slot counter and the kernel status, the last two zeroed before each launch.
-struct BatchCtl {
-  QueueCtl q;
-  unsigned long long head;
-  int kstatus;
-  int pad;
-};
-
-}  // namespace
-
-struct cvo_batch {
-  int n = 0;
-  int nblocks = 0;
-  int dp = 0, color_mode = 0;
-  std::vector<Plan*> plans;       // caller order
-  std::vector<int32_t> tgt, src;  // caller order
-  std::vector<int> team;          // caller order
-  std::vector<int> order;         // queue position -> caller index (largest work first)
-  SolveState* d_states = nullptr; // queue order
-  SolveState* h_states = nullptr; // pinned, queue order
-  QueueEntry* d_entries = nullptr;
-  BatchCtl* d_ctl = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  size_t bytes = 0;
-};
-
-struct cvo_ctx {
-  int device = 0;
-  int sms = 0;
-  cvo_params prm{};
-  size_t budget = 0, used = 0;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  std::vector<Cloud*> clouds;
-  std::map<std::pair<int, int>, Plan*> plans;
-  std::vector<cvo_batch*> batches;
-  Plan* eval_plan = nullptr;      // reused by cvo_eval
-  SolveState* h_state = nullptr;  // pinned
-  CloudStats* d_stats = nullptr;
-  CloudStats* h_stats = nullptr;  // pinned
-  int* h_int = nullptr;           // pinned scratch for small read-backs
-  std::string err;
-  std::mutex mu;
-};
-
-namespace {
+namespace cvo {
 
 int fail(cvo_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
   return code;
 }
 
-#define CK(call)                                                                   \
-  do {                                                                             \
-    cudaError_t e_ = (call);                                                       \
-    if (e_ != cudaSuccess)                                                         \
-      return fail(ctx, CVO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
 int dev_alloc(cvo_ctx* ctx, void** p, size_t bytes, size_t* acct) {
   *p = nullptr;
   if (ctx->budget > 0 && ctx->used + bytes > ctx->budget)
     return fail(ctx, CVO_ERR_OUT_OF_BUDGET, "HBM budget exhausted");
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return fail(ctx, CVO_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return fail(ctx, CVO_ERR_CUDA, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e));
   }
   ctx->used += bytes;
   if (acct) *acct += bytes;
   return CVO_OK;
+}
+
+void dev_free(cvo_ctx* ctx, void* p) {
+  if (p) cudaFreeAsync(p, ctx->stream);
 }
 
 void release_bytes(cvo_ctx* ctx, size_t bytes) { ctx->used -= bytes <= ctx->used ? bytes : ctx->used; }
@@ -182,24 +77,24 @@ Cloud* get_cloud(cvo_ctx* ctx, int32_t h) {
 }
 
 void free_grid(cvo_ctx* ctx, Grid& g) {
-  cudaFree(g.xyz);
-  cudaFree(g.feat);
-  cudaFree(g.cell_start);
+  dev_free(ctx, g.xyz);
+  dev_free(ctx, g.feat);
+  dev_free(ctx, g.cell_start);
   release_bytes(ctx, g.bytes);
   g = Grid();
 }
 
 void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
-  cudaFree(p->d_cfg);
-  cudaFree(p->d_iters);
-  cudaFree(p->d_state);
-  cudaFree(p->d_partials);
-  cudaFree(p->d_records);
-  cudaFree(p->seg_xs);
-  cudaFree(p->seg_pref);
-  cudaFree(p->cl_nseg);
-  cudaFree(p->cl_cand);
-  cudaFree(p->group_agg);
+  dev_free(ctx, p->d_cfg);
+  dev_free(ctx, p->d_iters);
+  dev_free(ctx, p->d_state);
+  dev_free(ctx, p->d_partials);
+  dev_free(ctx, p->d_records);
+  dev_free(ctx, p->seg_xs);
+  dev_free(ctx, p->seg_pref);
+  dev_free(ctx, p->cl_nseg);
+  dev_free(ctx, p->cl_cand);
+  dev_free(ctx, p->group_agg);
   release_bytes(ctx, p->bytes);
   p->d_cfg = nullptr;
   p->d_iters = nullptr;
@@ -222,13 +117,13 @@ void free_cloud(cvo_ctx* ctx, Cloud* c) {
   if (!c) return;
   for (Grid& g : c->grids) free_grid(ctx, g);
   for (Clusters& k : c->clusters) {
-    cudaFree(k.cstart);
+    dev_free(ctx, k.cstart);
     release_bytes(ctx, k.bytes);
   }
-  cudaFree(c->xyz);
-  cudaFree(c->feat);
-  cudaFree(c->zs);
-  cudaFree(c->zf);
+  dev_free(ctx, c->xyz);
+  dev_free(ctx, c->feat);
+  dev_free(ctx, c->zs);
+  dev_free(ctx, c->zf);
   release_bytes(ctx, c->bytes);
   delete c;
 }
@@ -265,7 +160,7 @@ int ensure_grid(cvo_ctx* ctx, Cloud* c, double h_req, int* index_out) {
   // built from the Morton-ordered copy: the stable cell sort keeps each cell's
   // points in Morton order, so consecutive candidates are spatially compact
   cudaError_t e = build_grid(c->zs, c->zf, n, c->dp, c->n_pad, nx, ny, nz, c->lo[0], c->lo[1],
-                             c->lo[2], hf, g.xyz, g.feat, g.cell_start, ctx->stream);
+                             c->lo[2], hf, g.xyz, g.feat, g.cell_start, ctx->pool, ctx->stream);
   if (e != cudaSuccess) {
     free_grid(ctx, g);
     return fail(ctx, CVO_ERR_CUDA, std::string("build_grid: ") + cudaGetErrorString(e));
@@ -289,30 +184,45 @@ int ensure_grid(cvo_ctx* ctx, Cloud* c, double h_req, int* index_out) {
   return CVO_OK;
 }
 
-// Source clusters whose octree nodes have edge <= max_edge (cached).
-int ensure_clusters(cvo_ctx* ctx, Cloud* c, float max_edge, int* index_out) {
-  for (size_t i = 0; i < c->clusters.size(); ++i)
-    if (c->clusters[i].max_edge == max_edge) {
-      *index_out = (int)i;
-      return CVO_OK;
-    }
-  Clusters k;
-  k.max_edge = max_edge;
-  int rc = dev_alloc(ctx, (void**)&k.cstart, sizeof(int) * (c->n + 2), &k.bytes);
-  if (rc != CVO_OK) return rc;
-  int* d_ncl = k.cstart + c->n + 1;
-  cudaError_t e = build_clusters(c->zs, (int)c->n, c->mf, max_edge, k.cstart, d_ncl, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->h_int, d_ncl, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+// Source clusters whose octree nodes have edge <= max_edges[l], one set per
+// level (cached per edge). Missing sets are built back to back and their
+// counts read with one synchronisation.
+int ensure_clusters(cvo_ctx* ctx, Cloud* c, const std::vector<float>& max_edges,
+                    std::vector<int>* index_out) {
+  index_out->assign(max_edges.size(), -1);
+  std::vector<size_t> built;   // indices into c->clusters built by this call
+  cudaError_t e = cudaSuccess;
+  for (size_t l = 0; l < max_edges.size(); ++l) {
+    for (size_t i = 0; i < c->clusters.size(); ++i)
+      if (c->clusters[i].max_edge == max_edges[l]) (*index_out)[l] = (int)i;
+    if ((*index_out)[l] >= 0) continue;
+    if ((int)built.size() >= kMaxLevels) return fail(ctx, CVO_ERR_INTERNAL, "too many levels");
+    Clusters k;
+    k.max_edge = max_edges[l];
+    int rc = dev_alloc(ctx, (void**)&k.cstart, sizeof(int) * (c->n + 2), &k.bytes);
+    if (rc != CVO_OK) return rc;
+    int* d_ncl = k.cstart + c->n + 1;
+    e = build_clusters(c->zs, (int)c->n, c->mf, k.max_edge, k.cstart, d_ncl, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->h_int + built.size(), d_ncl, sizeof(int), cudaMemcpyDeviceToHost,
+                          ctx->stream);
+    k.ncl = -1;   // filled after the synchronisation
+    c->clusters.push_back(k);
+    built.push_back(c->clusters.size() - 1);
+    (*index_out)[l] = (int)c->clusters.size() - 1;
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess && !built.empty()) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
-    cudaFree(k.cstart);
-    release_bytes(ctx, k.bytes);
+    for (size_t j = built.size(); j-- > 0;) {
+      Clusters& k = c->clusters[built[j]];
+      dev_free(ctx, k.cstart);
+      release_bytes(ctx, k.bytes);
+      c->clusters.erase(c->clusters.begin() + built[j]);
+    }
     return fail(ctx, CVO_ERR_CUDA, std::string("build_clusters: ") + cudaGetErrorString(e));
   }
-  k.ncl = *ctx->h_int;
-  c->clusters.push_back(k);
-  *index_out = (int)c->clusters.size() - 1;
+  for (size_t j = 0; j < built.size(); ++j) c->clusters[built[j]].ncl = ctx->h_int[j];
   return CVO_OK;
 }
 
@@ -390,8 +300,9 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   }
   SolveCfg cfg{};
   int ncl_max = 0;
+  std::vector<float> edges(hs.size());
   for (size_t l = 0; l < hs.size(); ++l) {
-    int gi = 0, ki = 0;
+    int gi = 0;
     int rc = ensure_grid(ctx, t, hs[l], &gi);
     if (rc != CVO_OK) return rc;
     cfg.grids[l] = t->grids[gi].view;
@@ -400,17 +311,21 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
     // i.e. at most 8 x 8 = kMaxSeg cell rows
     const double hh = t->grids[gi].view.h;
     const double rc_level = hs[l] / f;
-    const double edge = std::min(prm.cluster_factor * hh, (6.0 * hh - 2.21 * rc_level) / std::sqrt(3.0));
-    rc = ensure_clusters(ctx, s, (float)edge, &ki);
-    if (rc != CVO_OK) return rc;
-    cfg.clusters[l].cstart = s->clusters[ki].cstart;
-    cfg.clusters[l].ncl = s->clusters[ki].ncl;
-    ncl_max = std::max(ncl_max, s->clusters[ki].ncl);
+    edges[l] = (float)std::min(prm.cluster_factor * hh,
+                               (6.0 * hh - 2.21 * rc_level) / std::sqrt(3.0));
+  }
+  std::vector<int> ki;
+  int rc = ensure_clusters(ctx, s, edges, &ki);
+  if (rc != CVO_OK) return rc;
+  for (size_t l = 0; l < hs.size(); ++l) {
+    cfg.clusters[l].cstart = s->clusters[ki[l]].cstart;
+    cfg.clusters[l].ncl = s->clusters[ki[l]].ncl;
+    ncl_max = std::max(ncl_max, s->clusters[ki[l]].ncl);
   }
   const int per_sm = solve_blocks_per_sm(s->dp, prm.color_mode);
   if (per_sm <= 0) return fail(ctx, CVO_ERR_CUDA, "solve kernel cannot be resident");
   const int nblocks = std::min(per_sm * ctx->sms, 512);   // the tail reduction covers 512
-  int rc = reserve_plan(ctx, p, (int)ells.size(), ncl_max, nblocks);
+  rc = reserve_plan(ctx, p, (int)ells.size(), ncl_max, nblocks);
   if (rc != CVO_OK) return rc;
   std::vector<IterConst> ic(ells.size());
   const double log2e = 1.4426950408889634073599246810019;
@@ -503,7 +418,117 @@ int check_pose(cvo_ctx* ctx, const double* P) {
   return CVO_OK;
 }
 
-}  // namespace
+}  // namespace cvo
+
+namespace cvo {
+
+// Upload, check, centre, pack and Morton-order one cloud (the caller holds
+// the context lock). xyz / feat are host arrays, or device arrays read on
+// stream us when on_dev.
+int create_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, bool on_dev,
+                 cudaStream_t us, Cloud** out) {
+  *out = nullptr;
+  if (!xyz) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL xyz pointer");
+  if (n <= 0 || n > kMaxPoints) return fail(ctx, CVO_ERR_INVALID_ARG, "point count out of range");
+  const int D = ctx->prm.color_mode == CVO_COLOR_NONE ? 0 : ctx->prm.feat_dim;
+  if (D > 0 && !feat) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL feature pointer");
+  CK(cudaSetDevice(ctx->device));
+  if (!us) us = ctx->stream;
+  Cloud* c = new Cloud();
+  c->n = n;
+  c->n_pad = (int)((n + 31) / 32 * 32);
+  c->D = D;
+  c->dp = padded_dim(ctx->prm);
+  float *raw_xyz = nullptr, *raw_feat = nullptr;
+  int rc = CVO_OK;
+  auto cleanup = [&](int code) {
+    if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
+    if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    free_cloud(ctx, c);
+    return code;
+  };
+  // staging copy of the raw input (library-owned)
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&raw_xyz, sizeof(float) * 3 * n, ctx->pool, ctx->stream);
+  if (e == cudaSuccess && D > 0)
+    e = cudaMallocFromPoolAsync((void**)&raw_feat, sizeof(float) * D * n, ctx->pool, ctx->stream);
+  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  if (on_dev && us != ctx->stream) {
+    // order the caller's stream before our copies
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, us);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  }
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  e = cudaMemcpyAsync(raw_xyz, xyz, sizeof(float) * 3 * n, kind, ctx->stream);
+  if (e == cudaSuccess && D > 0)
+    e = cudaMemcpyAsync(raw_feat, feat, sizeof(float) * D * n, kind, ctx->stream);
+  if (e == cudaSuccess) e = cloud_stats(raw_xyz, raw_feat, (int)n, D, ctx->d_stats, ctx->pool, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(CloudStats), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  const CloudStats st = *ctx->h_stats;
+  if (st.bad) return cleanup(fail(ctx, CVO_ERR_INVALID_ARG, "cloud has a non-finite value"));
+  for (int a = 0; a < 3; ++a) {
+    c->c[a] = st.sum[a] / (double)n;
+    // bounding box in the centred frame, widened by a few ulps
+    const double lo = (double)st.lo[a] - c->c[a], hi = (double)st.hi[a] - c->c[a];
+    const double pad = 1e-6 * (1.0 + std::fabs(lo) + std::fabs(hi));
+    c->lo[a] = (float)(lo - pad);
+    c->hi[a] = (float)(hi + pad);
+  }
+  c->mf = morton_frame(c->lo, c->hi);
+  for (int cx = 0; cx < 2; ++cx)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cz = 0; cz < 2; ++cz) {
+        const double x = cx ? c->hi[0] : c->lo[0], y = cy ? c->hi[1] : c->lo[1],
+                     z = cz ? c->hi[2] : c->lo[2];
+        c->radius = std::max(c->radius, std::sqrt(x * x + y * y + z * z));
+      }
+  rc = dev_alloc(ctx, (void**)&c->xyz, sizeof(float4) * c->n_pad, &c->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&c->zs, sizeof(float4) * c->n_pad, &c->bytes);
+  if (rc == CVO_OK && c->dp > 0)
+    rc = dev_alloc(ctx, (void**)&c->feat, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
+  if (rc == CVO_OK && c->dp > 0)
+    rc = dev_alloc(ctx, (void**)&c->zf, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
+  if (rc != CVO_OK) return cleanup(rc);
+  e = pack_cloud(raw_xyz, raw_feat, (int)n, D, c->dp, c->n_pad, c->c[0], c->c[1], c->c[2],
+                 feature_scale(ctx->prm), c->xyz, c->feat, ctx->stream);
+  if (e == cudaSuccess)
+    e = morton_order(c->xyz, c->feat, (int)n, c->dp, c->n_pad, c->mf, c->zs, c->zf, ctx->pool,
+                     ctx->stream);
+  if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
+  if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
+  raw_xyz = raw_feat = nullptr;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
+  *out = c;
+  return CVO_OK;
+}
+
+// Register a cloud under a handle (reusing a free slot).
+int32_t add_cloud(cvo_ctx* ctx, Cloud* c) {
+  int32_t h = -1;
+  for (size_t i = 0; i < ctx->clouds.size(); ++i)
+    if (!ctx->clouds[i]) {
+      h = (int32_t)i;
+      break;
+    }
+  if (h < 0) {
+    h = (int32_t)ctx->clouds.size();
+    ctx->clouds.push_back(nullptr);
+  }
+  ctx->clouds[h] = c;
+  return h;
+}
+
+
+}  // namespace cvo
 
 extern "C" {
 
@@ -578,12 +603,25 @@ int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cv
   if (p.feat_dim == 0) ctx->prm.color_mode = CVO_COLOR_NONE;
   ctx->budget = hbm_budget_bytes;
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost((void**)&ctx->h_state, sizeof(SolveState)) != cudaSuccess ||
       cudaMallocHost((void**)&ctx->h_stats, sizeof(CloudStats)) != cudaSuccess ||
-      cudaMallocHost((void**)&ctx->h_int, sizeof(int) * 4) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_int, sizeof(int) * 2 * kMaxLevels) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_stats, sizeof(CloudStats)) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cvo_destroy(ctx);
+    return CVO_ERR_CUDA;
+  }
+  // a private stream-ordered pool that keeps freed memory for reuse: frees
+  // never wait for kernels on other streams (the request loop frees while its
+  // persistent kernel runs)
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  uint64_t keep = ~0ull;
+  if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess ||
+      cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+    ctx->pool = nullptr;
     cvo_destroy(ctx);
     return CVO_ERR_CUDA;
   }
@@ -594,6 +632,7 @@ int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cv
 int cvo_destroy(cvo_ctx* ctx) {
   if (!ctx) return CVO_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
+  serve_shutdown(ctx);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   while (!ctx->batches.empty()) destroy_batch(ctx, ctx->batches.back());
   for (auto& kv : ctx->plans) free_plan(ctx, kv.second);
@@ -605,7 +644,8 @@ int cvo_destroy(cvo_ctx* ctx) {
   if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
   if (ctx->h_int) cudaFreeHost(ctx->h_int);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
-  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);   // stream-ordered frees complete
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return CVO_OK;
@@ -615,98 +655,12 @@ int cvo_set_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, 
                   void* stream, int32_t* handle_out) {
   if (!ctx) return CVO_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  if (!xyz || !handle_out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL xyz or handle pointer");
-  if (n <= 0 || n > kMaxPoints) return fail(ctx, CVO_ERR_INVALID_ARG, "point count out of range");
-  const int D = ctx->prm.color_mode == CVO_COLOR_NONE ? 0 : ctx->prm.feat_dim;
-  if (D > 0 && !feat) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL feature pointer");
-  CK(cudaSetDevice(ctx->device));
-  cudaStream_t us = stream ? (cudaStream_t)stream : ctx->stream;
-  Cloud* c = new Cloud();
-  c->n = n;
-  c->n_pad = (int)((n + 31) / 32 * 32);
-  c->D = D;
-  c->dp = padded_dim(ctx->prm);
-  const bool on_dev = (flags & CVO_DEVICE_PTR) != 0;
-  float *raw_xyz = nullptr, *raw_feat = nullptr;
-  int rc = CVO_OK;
-  auto cleanup = [&](int code) {
-    if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
-    if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
-    cudaStreamSynchronize(ctx->stream);
-    free_cloud(ctx, c);
-    return code;
-  };
-  // staging copy of the raw input (library-owned)
-  cudaError_t e = cudaMallocAsync((void**)&raw_xyz, sizeof(float) * 3 * n, ctx->stream);
-  if (e == cudaSuccess && D > 0)
-    e = cudaMallocAsync((void**)&raw_feat, sizeof(float) * D * n, ctx->stream);
-  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
-  if (on_dev && us != ctx->stream) {
-    // order the caller's stream before our copies
-    cudaEvent_t ev;
-    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ev, us);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ev, 0);
-    cudaEventDestroy(ev);
-    if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
-  }
-  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  e = cudaMemcpyAsync(raw_xyz, xyz, sizeof(float) * 3 * n, kind, ctx->stream);
-  if (e == cudaSuccess && D > 0)
-    e = cudaMemcpyAsync(raw_feat, feat, sizeof(float) * D * n, kind, ctx->stream);
-  if (e == cudaSuccess) e = cloud_stats(raw_xyz, raw_feat, (int)n, D, ctx->d_stats, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(CloudStats), cudaMemcpyDeviceToHost,
-                        ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
-  const CloudStats st = *ctx->h_stats;
-  if (st.bad) return cleanup(fail(ctx, CVO_ERR_INVALID_ARG, "cloud has a non-finite value"));
-  for (int a = 0; a < 3; ++a) {
-    c->c[a] = st.sum[a] / (double)n;
-    // bounding box in the centred frame, widened by a few ulps
-    const double lo = (double)st.lo[a] - c->c[a], hi = (double)st.hi[a] - c->c[a];
-    const double pad = 1e-6 * (1.0 + std::fabs(lo) + std::fabs(hi));
-    c->lo[a] = (float)(lo - pad);
-    c->hi[a] = (float)(hi + pad);
-  }
-  c->mf = morton_frame(c->lo, c->hi);
-  for (int cx = 0; cx < 2; ++cx)
-    for (int cy = 0; cy < 2; ++cy)
-      for (int cz = 0; cz < 2; ++cz) {
-        const double x = cx ? c->hi[0] : c->lo[0], y = cy ? c->hi[1] : c->lo[1],
-                     z = cz ? c->hi[2] : c->lo[2];
-        c->radius = std::max(c->radius, std::sqrt(x * x + y * y + z * z));
-      }
-  rc = dev_alloc(ctx, (void**)&c->xyz, sizeof(float4) * c->n_pad, &c->bytes);
-  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&c->zs, sizeof(float4) * c->n_pad, &c->bytes);
-  if (rc == CVO_OK && c->dp > 0)
-    rc = dev_alloc(ctx, (void**)&c->feat, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
-  if (rc == CVO_OK && c->dp > 0)
-    rc = dev_alloc(ctx, (void**)&c->zf, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
-  if (rc != CVO_OK) return cleanup(rc);
-  e = pack_cloud(raw_xyz, raw_feat, (int)n, D, c->dp, c->n_pad, c->c[0], c->c[1], c->c[2],
-                 feature_scale(ctx->prm), c->xyz, c->feat, ctx->stream);
-  if (e == cudaSuccess)
-    e = morton_order(c->xyz, c->feat, (int)n, c->dp, c->n_pad, c->mf, c->zs, c->zf, ctx->stream);
-  if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
-  if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
-  raw_xyz = raw_feat = nullptr;
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
-  // reuse a free slot
-  int32_t h = -1;
-  for (size_t i = 0; i < ctx->clouds.size(); ++i)
-    if (!ctx->clouds[i]) {
-      h = (int32_t)i;
-      break;
-    }
-  if (h < 0) {
-    h = (int32_t)ctx->clouds.size();
-    ctx->clouds.push_back(nullptr);
-  }
-  ctx->clouds[h] = c;
-  *handle_out = h;
+  if (!handle_out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL handle pointer");
+  Cloud* c = nullptr;
+  const int rc = create_cloud(ctx, xyz, feat, n, (flags & CVO_DEVICE_PTR) != 0,
+                              (cudaStream_t)stream, &c);
+  if (rc != CVO_OK) return rc;
+  *handle_out = add_cloud(ctx, c);
   return CVO_OK;
 }
 
@@ -735,6 +689,8 @@ int cvo_eval(cvo_ctx* ctx, int32_t target, int32_t source, const double P[16], d
              cvo_eval_result* out) {
   if (!ctx) return CVO_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (serve_active(ctx))
+    return fail(ctx, CVO_ERR_BUSY, "the request loop is running (cvo_serve_stop ends it)");
   Cloud* t = get_cloud(ctx, target);
   Cloud* s = get_cloud(ctx, source);
   if (!t || !s) return fail(ctx, CVO_ERR_NOT_FOUND, "unknown cloud handle");
@@ -760,7 +716,7 @@ int cvo_eval(cvo_ctx* ctx, int32_t target, int32_t source, const double P[16], d
 
 }  // extern "C"
 
-namespace {
+namespace cvo {
 
 // Look up (or build) the solve plan of (target, source) and stage P0.
 int prepare_solve(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
@@ -802,7 +758,7 @@ void fill_stats(const SolveState* hs, cvo_stats* stats) {
   }
 }
 
-}  // namespace
+}  // namespace cvo
 
 extern "C" {
 
@@ -810,6 +766,8 @@ int cvo_align(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
               cvo_stats* stats) {
   if (!ctx) return CVO_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (serve_active(ctx))
+    return fail(ctx, CVO_ERR_BUSY, "the request loop is running (cvo_serve_stop ends it)");
   Plan* p = nullptr;
   int rc = prepare_solve(ctx, target, source, P0, P_out, &p);
   if (rc != CVO_OK) return rc;
@@ -826,6 +784,8 @@ int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double
                       int max_records, int* n_records) {
   if (!ctx) return CVO_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (serve_active(ctx))
+    return fail(ctx, CVO_ERR_BUSY, "the request loop is running (cvo_serve_stop ends it)");
   if (max_records > 0 && !records) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL records");
   Plan* p = nullptr;
   int rc = prepare_solve(ctx, target, source, P0, P_out, &p);
@@ -865,7 +825,7 @@ void* cvo_stream(cvo_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
 }  // extern "C"
 
-namespace {
+namespace cvo {
 
 // Estimated kept pairs of a whole solve, for team sizing: the source points
 // times the target's points per unit area (its bounding box read as a
@@ -916,9 +876,9 @@ void destroy_batch(cvo_ctx* ctx, cvo_batch* b) {
     if (Cloud* c = get_cloud(ctx, b->tgt[i])) c->refs -= 1;
     if (Cloud* c = get_cloud(ctx, b->src[i])) c->refs -= 1;
   }
-  cudaFree(b->d_states);
-  cudaFree(b->d_entries);
-  cudaFree(b->d_ctl);
+  dev_free(ctx, b->d_states);
+  dev_free(ctx, b->d_entries);
+  dev_free(ctx, b->d_ctl);
   if (b->h_states) cudaFreeHost(b->h_states);
   release_bytes(ctx, b->bytes);
   ctx->batches.erase(std::remove(ctx->batches.begin(), ctx->batches.end(), b),
@@ -932,7 +892,7 @@ int status_code(int bits) {
   return CVO_OK;
 }
 
-}  // namespace
+}  // namespace cvo
 
 extern "C" {
 
@@ -1062,6 +1022,8 @@ int cvo_batch_run(cvo_ctx* ctx, cvo_batch* b, const double* P0, double* P_out,
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!b || std::find(ctx->batches.begin(), ctx->batches.end(), b) == ctx->batches.end())
     return fail(ctx, CVO_ERR_NOT_FOUND, "unknown batch");
+  if (serve_active(ctx))
+    return fail(ctx, CVO_ERR_BUSY, "the request loop is running (cvo_serve_stop ends it)");
   if (!P0 || !P_out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL pose array");
   for (int i = 0; i < b->n; ++i) {
     const int rc = check_pose(ctx, P0 + 16 * (size_t)i);

@@ -106,7 +106,8 @@ struct SolveState {
   unsigned long long nnz_pass[2], cand_pass[2];
   unsigned long long nnz_eval, cand_eval;   // gradient pass of the last iteration
   unsigned int bar_count, bar_gen;          // grid barrier (zeroed before each launch)
-  unsigned int join_count, pad_join;        // queued solves: blocks of the team that have started
+  unsigned int join_count, leave_count;     // queued solves: blocks of the team that have started
+                                            // and that are done with the entry
   unsigned long long t_begin_ns, t_end_ns;  // global timer at the start and end of the solve
   double red_sums[10];                      // pass totals published by the barrier's last block
 };
@@ -138,7 +139,9 @@ struct QueueEntry {
   const SolveCfg* cfg;
   SolveState* st;            // zeroed, with P0 set, before the entry is published
   double* partials;          // 2 * team * kPartialStride doubles
-  PairResult* out;           // NULL: the host reads st after the launch
+  PairResult* out;           // NULL: the host reads st after the launch; else written by the
+                             // team's last block to finish, so that no block of the team
+                             // touches the entry once out->done is set
   int team, slot0;
 };
 
@@ -151,9 +154,10 @@ struct QueueCtl {
 };
 
 // ---- grid.cu --------------------------------------------------------------
+// Temporaries are drawn from `pool`, stream-ordered on s.
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int n, int bits,
-                             cudaStream_t s);
+                             cudaMemPool_t pool, cudaStream_t s);
 
 struct CloudStats {
   double sum[3];
@@ -163,7 +167,7 @@ struct CloudStats {
 };
 // FP64 sum, FP32 bounding box and a non-finite check of a raw cloud.
 cudaError_t cloud_stats(const float* xyz, const float* feat, int n, int D,
-                        CloudStats* d_out, cudaStream_t s);
+                        CloudStats* d_out, cudaMemPool_t pool, cudaStream_t s);
 
 // Centre, pack (float4 xyz) and pre-scale features into dp SoA planes.
 cudaError_t pack_cloud(const float* xyz, const float* feat, int n, int D, int dp, int n_pad,
@@ -181,7 +185,7 @@ MortonFrame morton_frame(const float lo[3], const float hi[3]);
 // Reorder a packed cloud along a Morton curve of its bounding box.
 cudaError_t morton_order(const float4* xyz, const float* feat, int n, int dp, int n_pad,
                          const MortonFrame& mf, float4* out_xyz, float* out_feat,
-                         cudaStream_t s);
+                         cudaMemPool_t pool, cudaStream_t s);
 
 // Cut a Morton-ordered cloud into clusters: runs sharing the Morton prefix of
 // an octree node with edge <= max_edge, split into runs of <= kClusterMax.
@@ -192,7 +196,8 @@ cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, floa
 // Build a cell list of edge h over a packed cloud.
 cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int n_pad,
                        int nx, int ny, int nz, float ox, float oy, float oz, float h,
-                       float4* out_xyz, float* out_feat, int* cell_start, cudaStream_t s);
+                       float4* out_xyz, float* out_feat, int* cell_start, cudaMemPool_t pool,
+                       cudaStream_t s);
 
 // ---- pair_kernels.cu -------------------------------------------------------
 // The whole solve (or one evaluation, cfg->mode == kModeEval) as one

@@ -341,13 +341,14 @@ inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
 }  // namespace
 
-cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int n, int bits, cudaStream_t s) {
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int n, int bits, cudaMemPool_t pool,
+                             cudaStream_t s) {
   if (n <= 1) return cudaSuccess;
   const int nb = blocks_for(n, kSortTile);
   uint32_t *k2 = nullptr, *v2 = nullptr, *hist = nullptr;
-  cudaError_t e = cudaMallocAsync(&k2, sizeof(uint32_t) * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&v2, sizeof(uint32_t) * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&hist, sizeof(uint32_t) * 256 * nb, s);
+  cudaError_t e = cudaMallocFromPoolAsync(&k2, sizeof(uint32_t) * n, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&v2, sizeof(uint32_t) * n, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&hist, sizeof(uint32_t) * 256 * nb, pool, s);
   uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
   const int passes = (bits + 7) / 8;
   for (int p = 0; p < passes && e == cudaSuccess; ++p) {
@@ -371,15 +372,15 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int n, int bits, cu
 }
 
 cudaError_t cloud_stats(const float* xyz, const float* feat, int n, int D, CloudStats* d_out,
-                        cudaStream_t s) {
+                        cudaMemPool_t pool, cudaStream_t s) {
   const int nb = min(1024, blocks_for(n, kStatThreads));
   double* psum = nullptr;
   float *plo = nullptr, *phi = nullptr;
   int* pbad = nullptr;
-  cudaError_t e = cudaMallocAsync(&psum, sizeof(double) * 3 * nb, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&plo, sizeof(float) * 3 * nb, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&phi, sizeof(float) * 3 * nb, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&pbad, sizeof(int) * nb, s);
+  cudaError_t e = cudaMallocFromPoolAsync(&psum, sizeof(double) * 3 * nb, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&plo, sizeof(float) * 3 * nb, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&phi, sizeof(float) * 3 * nb, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&pbad, sizeof(int) * nb, pool, s);
   if (e == cudaSuccess) {
     stats_partial_kernel<<<nb, kStatThreads, 0, s>>>(xyz, feat, n, D, psum, plo, phi, pbad);
     stats_final_kernel<<<1, 32, 0, s>>>(psum, plo, phi, pbad, nb, d_out);
@@ -411,18 +412,18 @@ MortonFrame morton_frame(const float lo[3], const float hi[3]) {
 
 cudaError_t morton_order(const float4* xyz, const float* feat, int n, int dp, int n_pad,
                          const MortonFrame& mf, float4* out_xyz, float* out_feat,
-                         cudaStream_t s) {
+                         cudaMemPool_t pool, cudaStream_t s) {
   const float* lo = mf.lo;
   const float scale = mf.scale;
   uint32_t *keys = nullptr, *vals = nullptr;
-  cudaError_t e = cudaMallocAsync(&keys, sizeof(uint32_t) * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&vals, sizeof(uint32_t) * n, s);
+  cudaError_t e = cudaMallocFromPoolAsync(&keys, sizeof(uint32_t) * n, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&vals, sizeof(uint32_t) * n, pool, s);
   if (e == cudaSuccess) {
     morton_keys_kernel<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, lo[0], lo[1], lo[2], scale,
                                                           keys, vals);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, 30, s);
+  if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, 30, pool, s);
   if (e == cudaSuccess) {
     gather_kernel<<<blocks_for(n_pad, 256), 256, 0, s>>>(xyz, feat, vals, n, dp, n_pad, out_xyz,
                                                          out_feat);
@@ -450,19 +451,19 @@ cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, floa
 
 cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int n_pad, int nx,
                        int ny, int nz, float ox, float oy, float oz, float h, float4* out_xyz,
-                       float* out_feat, int* cell_start, cudaStream_t s) {
+                       float* out_feat, int* cell_start, cudaMemPool_t pool, cudaStream_t s) {
   const int ncells = nx * ny * nz;
   int bits = 1;
   while (bits < 32 && (1u << bits) < (uint32_t)ncells) ++bits;
   uint32_t *keys = nullptr, *vals = nullptr;
-  cudaError_t e = cudaMallocAsync(&keys, sizeof(uint32_t) * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(&vals, sizeof(uint32_t) * n, s);
+  cudaError_t e = cudaMallocFromPoolAsync(&keys, sizeof(uint32_t) * n, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&vals, sizeof(uint32_t) * n, pool, s);
   if (e == cudaSuccess) {
     cell_keys_kernel<<<blocks_for(n, 256), 256, 0, s>>>(xyz, n, nx, ny, nz, ox, oy, oz, 1.0f / h,
                                                         keys, vals);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, bits, s);
+  if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, bits, pool, s);
   if (e == cudaSuccess) {
     gather_kernel<<<blocks_for(n_pad, 256), 256, 0, s>>>(xyz, feat, vals, n, dp, n_pad, out_xyz,
                                                          out_feat);

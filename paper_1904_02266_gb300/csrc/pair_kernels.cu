@@ -1184,21 +1184,21 @@ __device__ void claim_slot(const QueueEntry* entries, const QueueCtl* ctl,
   *entry_out = -1;
 }
 
-// Solve results for the host: written by the team's first block once the
-// solve is published, the done flag last (release at system scope).
+// Solve results for the host, read at L2 (the team's first block published
+// them), the done flag last (release at system scope).
 __device__ void write_result(const SolveState* st, PairResult* out) {
-  for (int i = 0; i < 16; ++i) out->P[i] = st->P[i];
-  out->F = st->F;
-  out->t = st->t;
-  out->ell = st->ell;
-  out->device_ms = (double)(st->t_end_ns - st->t_begin_ns) * 1e-6;
-  out->pair_evals = (long long)st->nnz_total;
-  out->candidates = (long long)st->cand_total;
-  out->iters = st->iter;
-  out->converged = st->converged;
-  out->fallback_steps = st->fallback_steps;
-  out->no_ascent_steps = st->no_ascent_steps;
-  out->status = st->status;
+  for (int i = 0; i < 16; ++i) out->P[i] = __ldcg(&st->P[i]);
+  out->F = __ldcg(&st->F);
+  out->t = __ldcg(&st->t);
+  out->ell = __ldcg(&st->ell);
+  out->device_ms = (double)(__ldcg(&st->t_end_ns) - __ldcg(&st->t_begin_ns)) * 1e-6;
+  out->pair_evals = (long long)__ldcg(&st->nnz_total);
+  out->candidates = (long long)__ldcg(&st->cand_total);
+  out->iters = __ldcg(&st->iter);
+  out->converged = __ldcg(&st->converged);
+  out->fallback_steps = __ldcg(&st->fallback_steps);
+  out->no_ascent_steps = __ldcg(&st->no_ascent_steps);
+  out->status = __ldcg(&st->status);
   __threadfence_system();
   st_release_sys_s32(&out->done, 1);
 }
@@ -1226,8 +1226,10 @@ queue_kernel(const QueueEntry* __restrict__ entries, const QueueCtl* __restrict_
     const QueueEntry en = load_entry(entries + sm.q_entry);
     const Team team{(int)(sm.q_slot - en.slot0), en.team};
     solve_pair<DP, MODE, DPS, NU>(en.cfg, en.st, en.partials, nullptr, team, sm, true);
-    if (team.rank == 0 && threadIdx.x == 0) {
-      if (en.out) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned left = atomicAdd(&en.st->leave_count, 1u);
+      if (left == (unsigned)en.team - 1 && en.out) {
         __threadfence();
         write_result(en.st, en.out);
       }

@@ -297,3 +297,53 @@ def room_pair(n_points=20000, seed=None, deg=3.0, meters=0.03, mode="gradient", 
     return {"X": X.astype(np.float32), "FX": FX.astype(np.float32),
             "Z": Z.astype(np.float32), "FZ": FZ.astype(np.float32),
             "P_gt": M, "seed": seed}
+
+
+# --------------------------------------------------------------------------
+# config 5: camera streams served against resident keyframes
+# --------------------------------------------------------------------------
+
+def stream_keyframe(kf_seed: int, n_kf: int, noise=0.005):
+    """Keyframe of one stream: points on the textured planes of kf_seed."""
+    rng = np.random.default_rng(kf_seed)
+    tex = _PlaneTextures(rng)
+    X, FX = _sample_planes(rng, tex, n_kf, noise)
+    return X.astype(np.float32), FX.astype(np.float32)
+
+
+def stream_frame(kf_seed: int, frame: int, n: int, deg=3.0, meters=0.03, noise=0.005):
+    """Frame `frame` of a keyframe's epoch: a fresh sample of the same textured
+    planes moved by its own seeded motion. Returns (Z, FZ, P_gt)."""
+    rng = np.random.default_rng(kf_seed)
+    tex = _PlaneTextures(rng)
+    rng2 = np.random.default_rng([kf_seed, frame])
+    Zw, FZ = _sample_planes(rng2, tex, n, noise)
+    M = random_motion(rng2, deg, meters)
+    return transform(M, Zw).astype(np.float32), FZ.astype(np.float32), inverse(M)
+
+
+def serving_trace(n_streams=64, rate_hz=30.0, duration_s=20.0, n_range=(5000, 60000),
+                  keyframe_every=10, seed=None):
+    """Open-loop arrivals of camera frames: per stream, exponential
+    inter-arrival times of mean 1/rate_hz (Poisson), frame sizes uniform in
+    n_range, a new keyframe (of its own size in n_range) every keyframe_every
+    frames. Returns the requests sorted by arrival time, each a dict with
+    t (s), stream, kf_seed, n_kf, frame (index in the keyframe's epoch), n."""
+    seed = seed_for(5) if seed is None else seed
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n_streams):
+        t = float(rng.exponential(1.0 / rate_hz))
+        k = 0
+        kf_seed = n_kf = None
+        while t < duration_s:
+            if k % keyframe_every == 0:
+                kf_seed = seed * 100003 + s * 1009 + k
+                n_kf = int(rng.integers(n_range[0], n_range[1] + 1))
+            out.append({"t": t, "stream": s, "kf_seed": kf_seed, "n_kf": n_kf,
+                        "frame": k % keyframe_every, "n": int(rng.integers(n_range[0],
+                                                                        n_range[1] + 1))})
+            k += 1
+            t += float(rng.exponential(1.0 / rate_hz))
+    out.sort(key=lambda r: r["t"])
+    return out
