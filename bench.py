@@ -11,6 +11,16 @@ Metric: pair evaluations per second (Gpairs/s). A pair evaluation is one kept
 (in-cutoff) (i, j) pair in one gradient or step pass. frame_pairs_per_s is
 reported beside it.
 
+Two more measurements ride on the same line at N = 1 (each against plain
+one-pair-at-a-time solves of the same work, with the largest pose difference
+between the two):
+  batch    256 uneven pairs (planes, 2k-40k points, own ell0 each) solved by
+           one persistent launch replayed from a CUDA graph (cvo_batch_run);
+  serving  an open-loop trace of 64 camera streams at 30 Hz (Poisson arrivals,
+           frames of 5k-60k points, a new keyframe every 10 frames) for
+           --serve-seconds of arrivals, through cvo_submit / cvo_poll, with
+           p50 / p99 latency from arrival to result.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cvo|reference]
 
 For N > 1 launch under torch.distributed.run. Every rank solves its own copy
@@ -68,6 +78,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=0.5)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -306,6 +320,11 @@ def run_cvo(args, world, rank, local):
                      "phase_ms_per_solve": phases},
         "clocks": clocks,
     }
+    ctx.close()
+    if world == 1 and not args.no_batch:
+        line["batch"] = bench_batch(cvo, torch, local, args.batch_pairs, flush)
+    if world == 1 and not args.no_serve:
+        line["serving"] = bench_serving(cvo, args.serve_seconds)
     if not args.no_cpu_baseline and world == 1:
         v, cores, dt, cp = cpu_baseline_sample(d, 6)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -313,9 +332,161 @@ def run_cvo(args, world, rank, local):
                                           f"FP64 all-pairs oracle ({cp} kept pair evals, "
                                           f"{dt:.1f} s)"}
     print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _events(torch, stream):
+    return (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+
+def bench_batch(cvo, torch, local, n_pairs, flush):
+    """Uneven pairs in one persistent launch vs one plain solve per pair."""
+    pairs = synth.batch_pairs(n_pairs=n_pairs, seed=synth.seed_for(3))
+    ell0 = [d["ell0"] for d in pairs]
+    P0 = np.stack([np.eye(4)] * n_pairs)
+    with cvo.Context(device=local) as ctx:
+        hs = [(ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])) for d in pairs]
+        stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
+        with ctx.batch([t for t, _ in hs], [s for _, s in hs], ell0=ell0) as b:
+            info = b.info()
+            b.run(P0)
+            ms = []
+            for _ in range(3):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                    e0, e1 = _events(torch, stream)
+                    e0.record(stream)
+                P, st = b.run(P0)
+                with torch.cuda.stream(stream):
+                    e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+    t_batch = min(ms)
+    pe = sum(x["pair_evals"] for x in st)
+    plain_ms, plain_pe, worst = 0.0, 0, 0.0
+    for i, d in enumerate(pairs):
+        with cvo.Context(device=local, ell0=ell0[i]) as c2:
+            t, s = c2.set_cloud(d["X"], d["FX"]), c2.set_cloud(d["Z"], d["FZ"])
+            c2.align(t, s)
+            st2 = torch.cuda.ExternalStream(c2.stream, device=torch.device("cuda", local))
+            e0, e1 = _events(torch, st2)
+            e0.record(st2)
+            Pp, sp = c2.align(t, s)
+            e1.record(st2)
+            e1.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+            plain_pe += sp["pair_evals"]
+            worst = max(worst, *synth_pose_err(P[i], Pp))
+    return {"workload": f"{n_pairs} uneven planes pairs, 2k-40k points, motions <= 5 deg / 5 cm, "
+                        f"ell0 ~ U[0.12, 0.18]",
+            "ms_per_batch": t_batch, "frame_pairs_per_s": n_pairs / (t_batch * 1e-3),
+            "gpairs_per_s": pe / (t_batch * 1e-3) / 1e9, "blocks": info["blocks"],
+            "max_team": info["max_team"], "graph": info["graph"],
+            "plain": {"ms": plain_ms, "frame_pairs_per_s": n_pairs / (plain_ms * 1e-3),
+                      "gpairs_per_s": plain_pe / (plain_ms * 1e-3) / 1e9},
+            "max_pose_diff_vs_plain": worst}
+
+
+def _serve_trace(seconds):
+    trace = synth.serving_trace(n_streams=64, rate_hz=30.0, duration_s=seconds,
+                                n_range=(5000, 60000), keyframe_every=10)
+    kfs, frames = {}, []
+    for r in trace:
+        if r["kf_seed"] not in kfs:
+            kfs[r["kf_seed"]] = synth.stream_keyframe(r["kf_seed"], r["n_kf"])
+        frames.append(synth.stream_frame(r["kf_seed"], r["frame"], r["n"]))
+    prev = {}
+    for r in trace:   # the keyframe each keyframe replaces (to release it)
+        seq = prev.setdefault(r["stream"], [])
+        if not seq or seq[-1] != r["kf_seed"]:
+            r["replaces"] = seq[-1] if seq else None
+            seq.append(r["kf_seed"])
+        else:
+            r["replaces"] = None
+    return trace, kfs, frames
+
+
+def _serve_run(cvo, trace, kfs, frames):
+    """Replay the trace through the request loop. Latency: arrival to poll."""
+    res = [None] * len(trace)
+    with cvo.Context(device=0) as ctx:
+        ctx.serve_start()
+        handles, open_, retiring, tickets = {}, {}, set(), {}
+        arr = [r["t"] for r in trace]
+        i = 0
+        t0 = time.perf_counter()
+        while i < len(trace) or tickets:
+            now = time.perf_counter() - t0
+            while i < len(trace) and arr[i] <= now:
+                r = trace[i]
+                ks = r["kf_seed"]
+                if ks not in handles:
+                    handles[ks] = ctx.set_cloud(*kfs[ks])
+                    open_[ks] = 0
+                    if r["replaces"] is not None:
+                        retiring.add(r["replaces"])
+                tickets[ctx.submit(handles[ks], frames[i][0], frames[i][1])] = i
+                open_[ks] += 1
+                i += 1
+            for t in list(tickets):
+                out = ctx.poll(t)
+                if out is not None:
+                    j = tickets.pop(t)
+                    res[j] = (out[0], out[1], time.perf_counter() - t0 - arr[j])
+                    open_[trace[j]["kf_seed"]] -= 1
+            for ks in list(retiring):
+                if open_.get(ks, 1) == 0:
+                    ctx.release(handles.pop(ks))
+                    retiring.discard(ks)
+            time.sleep(0.0002)
+        span = time.perf_counter() - t0
+        ctx.serve_stop()
+    return res, span
+
+
+def _plain_run(cvo, trace, kfs, frames):
+    """The same trace solved one request at a time in arrival order."""
+    res = [None] * len(trace)
+    with cvo.Context(device=0) as ctx:
+        handles = {}
+        t0 = time.perf_counter()
+        for i, r in enumerate(trace):
+            now = time.perf_counter() - t0
+            if now < r["t"]:
+                time.sleep(r["t"] - now)
+            ks = r["kf_seed"]
+            if ks not in handles:
+                handles[ks] = ctx.set_cloud(*kfs[ks])
+                if r["replaces"] is not None and r["replaces"] in handles:
+                    ctx.release(handles.pop(r["replaces"]))
+            s = ctx.set_cloud(frames[i][0], frames[i][1])
+            P, st = ctx.align(handles[ks], s)
+            ctx.release(s)
+            res[i] = (P, st, time.perf_counter() - t0 - r["t"])
+        span = time.perf_counter() - t0
+    return res, span
+
+
+def bench_serving(cvo, seconds):
+    trace, kfs, frames = _serve_trace(seconds)
+
+    def summary(res, span):
+        lat = np.array([x[2] * 1e3 for x in res])
+        return {"frame_pairs_per_s": len(res) / span,
+                "gpairs_per_s": sum(x[1]["pair_evals"] for x in res) / span / 1e9,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "failed": int(sum(1 for x in res if x[1]["status"] != 0))}
+
+    rs, ss = _serve_run(cvo, trace, kfs, frames)
+    rp, sp = _plain_run(cvo, trace, kfs, frames)
+    out = summary(rs, ss)
+    out["workload"] = (f"{len(trace)} requests: 64 streams x 30 Hz (Poisson) for {seconds} s, "
+                       f"planes frames 5k-60k points vs resident keyframes renewed every 10 frames")
+    out["latency"] = "arrival to result, open loop (offered load above capacity: queueing included)"
+    out["plain"] = summary(rp, sp)
+    out["max_pose_diff_vs_plain"] = max(max(synth_pose_err(a[0], b[0])) for a, b in zip(rs, rp))
+    return out
 
 
 def recorded_traffic(kernel: str):
