@@ -90,6 +90,10 @@ typedef struct {
                               capped so a cluster spans at most 8 x 8 cell rows; 2.0 */
     int cost_chunk;        /* work split: per-chunk overhead in pair-test units; 24 */
     int cost_cluster;      /* work split: cost of staging one cluster in pair-test units; 64 */
+    double cost_kept;      /* work split of a reused plan: cost of a kept pair in pair-test
+                              units, from the kept pairs counted by the plan's first gradient
+                              pass (the split is redone once, at the plan's second iteration);
+                              0 disables the rebalance; 0 */
     double team_factor;    /* batches and served requests: a pair's team gets about
                               team_factor * (its share of the estimated pair work) of the
                               blocks, at least one; 6.0 */

@@ -65,7 +65,7 @@ class cvo_params(ctypes.Structure):
                 ("step_order", ctypes.c_int), ("feat_dim", ctypes.c_int),
                 ("cell_factor", ctypes.c_double), ("cluster_factor", ctypes.c_double),
                 ("cost_chunk", ctypes.c_int), ("cost_cluster", ctypes.c_int),
-                ("team_factor", ctypes.c_double)]
+                ("cost_kept", ctypes.c_double), ("team_factor", ctypes.c_double)]
 
 
 class cvo_eval_result(ctypes.Structure):

@@ -94,6 +94,7 @@ void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
   dev_free(ctx, p->seg_pref);
   dev_free(ctx, p->cl_nseg);
   dev_free(ctx, p->cl_cand);
+  dev_free(ctx, p->cl_kept);
   dev_free(ctx, p->group_agg);
   release_bytes(ctx, p->bytes);
   p->d_cfg = nullptr;
@@ -101,7 +102,7 @@ void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
   p->d_state = nullptr;
   p->d_partials = nullptr;
   p->d_records = nullptr;
-  p->seg_xs = p->seg_pref = p->cl_nseg = p->cl_cand = nullptr;
+  p->seg_xs = p->seg_pref = p->cl_nseg = p->cl_cand = p->cl_kept = nullptr;
   p->group_agg = nullptr;
   p->bytes = 0;
   p->cap_iters = p->cap_ncl = 0;
@@ -268,6 +269,7 @@ int reserve_plan(cvo_ctx* ctx, Plan* p, int iters, int ncl, int nblocks) {
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->seg_pref, sizeof(int) * (size_t)ncl * kMaxSeg, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_nseg, sizeof(int) * ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_cand, sizeof(int) * ncl, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_kept, sizeof(int) * ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->group_agg, sizeof(long long) * ng, &p->bytes);
   if (rc != CVO_OK) {
     free_plan_buffers(ctx, p);
@@ -348,10 +350,12 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   cfg.seg_pref = p->seg_pref;
   cfg.cl_nseg = p->cl_nseg;
   cfg.cl_cand = p->cl_cand;
+  cfg.cl_kept = p->cl_kept;
   cfg.group_agg = p->group_agg;
   cfg.src_radius = s->radius;
   cfg.cost_chunk = prm.cost_chunk;
   cfg.cost_cluster = prm.cost_cluster;
+  cfg.cost_kept = (float)prm.cost_kept;
   for (int a = 0; a < 3; ++a) {
     cfg.cX[a] = t->c[a];
     cfg.cZ[a] = s->c[a];
@@ -555,6 +559,7 @@ void cvo_params_default(cvo_params* p) {
   p->cluster_factor = 2.0;
   p->cost_chunk = 24;
   p->cost_cluster = 64;
+  p->cost_kept = 0.0;
   p->team_factor = 6.0;
 }
 
@@ -591,7 +596,8 @@ int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cv
                   p.cell_factor >= 0.5 && p.cell_factor <= 8.0 && std::isfinite(p.ell0) &&
                   p.cluster_factor > 0.0 && p.cluster_factor <= 8.0 && p.cost_chunk >= 0 &&
                   p.cost_chunk <= 4096 && p.cost_cluster >= 0 && p.cost_cluster <= 65536 &&
-                  p.team_factor > 0.0 && p.team_factor <= 1024.0;
+                  p.team_factor > 0.0 && p.team_factor <= 1024.0 && p.cost_kept >= 0.0 &&
+                  p.cost_kept <= 1024.0;
   if (!ok) return CVO_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)

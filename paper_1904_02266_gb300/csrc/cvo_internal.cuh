@@ -75,10 +75,12 @@ struct SolveCfg {
   int* seg_pref;           // candidate offset of each segment in its cluster
   int* cl_nseg;            // segments per cluster
   int* cl_cand;            // candidates per cluster
+  int* cl_kept;            // kept pairs per cluster in the first gradient pass of a plan
   long long* group_agg;    // work of each group of 32 consecutive clusters
   double src_radius;       // max |z'| over the centred source (bounds pose drift)
   int cost_chunk;          // work model: a chunk costs cs4 + cost_chunk pair tests,
-  int cost_cluster;        //   staging a cluster cost_cluster
+  int cost_cluster;        //   staging a cluster cost_cluster, and once kept pairs are
+  float cost_kept;         //   known cost_kept per kept pair (spread over the chunks)
   double cX[3], cZ[3];     // FP64 centroids
   double sigma2, a2, b2;
   double ell_floor, eps_pose, eps_grad;

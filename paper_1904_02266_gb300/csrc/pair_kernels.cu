@@ -35,6 +35,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "cvo_internal.cuh"
 
 // Resident blocks per SM the solve kernel is compiled for (register budget).
@@ -100,7 +102,18 @@ struct Team {
   int rank, size;
 };
 
+// Scalars of the solve configuration that the FP64 tail reads every
+// iteration, copied once per solve so that the tail issues no dependent
+// global loads.
+struct TailConst {
+  double cX[3], cZ[3];
+  double sigma2, inv_a2, inv_b2;
+  double ell_floor, eps_pose, eps_grad, src_radius;
+  int mode, step_order, max_iters;
+};
+
 struct BlockCtx {
+  TailConst tc;
   double P[16];           // current pose
   double Rp[9], Tp[3];    // centred pose at the last plan
   double xi[6];
@@ -110,6 +123,7 @@ struct BlockCtx {
   double ell, inv_l2, r_plan, plan_ell;
   int k, level, plan_level;
   int need_plan, done, converged, fallback, no_ascent, have_t_prev;
+  int use_kept, collect_kept, rebalance;   // kept-pair weighting of the work split
   unsigned long long nnz_total, cand_total, nnz_grad, cand_grad;
   float R[9], T[3];       // FP32 centred pose: z~' = R z' + T
   float om[3], vc[3];     // unit step direction (centred frame)
@@ -124,30 +138,29 @@ __device__ __forceinline__ void cross3d(const double a[3], const double b[3], do
 }
 
 // Centred pose in FP64: R and T' = R cZ + T - cX.
-__device__ void centred_pose(const SolveCfg* cfg, const double P[16], double R[9], double T[3]) {
+__device__ void centred_pose(const TailConst& tc, const double P[16], double R[9], double T[3]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    double tr = P[4 * r + 3] - cfg->cX[r];
+    double tr = P[4 * r + 3] - tc.cX[r];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       R[3 * r + c] = P[4 * r + c];
-      tr = fma(P[4 * r + c], cfg->cZ[c], tr);
+      tr = fma(P[4 * r + c], tc.cZ[c], tr);
     }
     T[r] = tr;
   }
 }
 
-// Iteration k's constants from the host table, the FP32 pose, and whether the
-// traversal plan must be rebuilt.
-__device__ void begin_iteration(const SolveCfg* cfg, BlockCtx& b) {
-  const IterConst ic = cfg->iters[b.k];
+// Iteration k's constants (ic = the host table's entry k), the FP32 pose, and
+// whether the traversal plan must be rebuilt.
+__device__ void begin_iteration(const IterConst& ic, BlockCtx& b) {
   b.ell = ic.ell;
   b.inv_l2 = ic.inv_l2;
   b.A = ic.A;
   b.rc2 = ic.rc2;
   b.inv_l2f = (float)ic.inv_l2;
   double R[9], T[3];
-  centred_pose(cfg, b.P, R, T);
+  centred_pose(b.tc, b.P, R, T);
 #pragma unroll
   for (int i = 0; i < 9; ++i) b.R[i] = (float)R[i];
 #pragma unroll
@@ -158,13 +171,17 @@ __device__ void begin_iteration(const SolveCfg* cfg, BlockCtx& b) {
   // ell shrinks a fresh, tighter plan costs less than the extra candidates
   bool replan = b.need_plan || ic.level != b.plan_level || ic.ell != b.plan_ell;
   if (!replan) {
-    double dr = 0.0, dt = 0.0;
+    double d2r[9], d2t[3];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) dr += (R[i] - b.Rp[i]) * (R[i] - b.Rp[i]);
+    for (int i = 0; i < 9; ++i) d2r[i] = (R[i] - b.Rp[i]) * (R[i] - b.Rp[i]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dt += (T[i] - b.Tp[i]) * (T[i] - b.Tp[i]);
+    for (int i = 0; i < 3; ++i) d2t[i] = (T[i] - b.Tp[i]) * (T[i] - b.Tp[i]);
+    // pairwise sums: short dependent chains (FP64 latency dominates the tail)
+    const double dr = ((d2r[0] + d2r[1]) + (d2r[2] + d2r[3])) +
+                      ((d2r[4] + d2r[5]) + (d2r[6] + d2r[7])) + d2r[8];
+    const double dt = (d2t[0] + d2t[1]) + d2t[2];
     // |dR z + dT| <= |dR|_F |z| + |dT| for every source point, |z| <= r_src
-    const double drift = ((double)sqrtf((float)dr) * cfg->src_radius + (double)sqrtf((float)dt)) *
+    const double drift = ((double)sqrtf((float)dr) * b.tc.src_radius + (double)sqrtf((float)dt)) *
                              (1.0 + 1e-5) + 1e-6 * need;
     replan = (need + drift > b.r_plan) || (b.r_plan > kLoose * (need + drift));
   }
@@ -182,62 +199,98 @@ __device__ void begin_iteration(const SolveCfg* cfg, BlockCtx& b) {
   }
 }
 
+// FP64 reciprocal from the FP32 one and two Newton steps r <- r (2 - x r)
+// (each squares the relative error: 1e-7 -> 1e-14 -> 1e-28). Finite,
+// nonzero x within FP32 range.
+__device__ __forceinline__ double recip_refined(double x) {
+  double r = (double)(1.0f / (float)x);
+  r = r * fma(-x, r, 2.0);
+  r = r * fma(-x, r, 2.0);
+  return r;
+}
+
 // Smallest positive t at which G'(t) = c0 + c1 t + c2 t^2 + c3 t^3 changes sign
 // from + to - (the first local maximum of the quartic model, Sec. 4 "Step
 // size"), given c0 = S1 > 0. With three real roots r1 < r2 < r3 the sign
 // pattern of G' decides: for c3 < 0 the + -> - crossings are r1 and r3, for
 // c3 > 0 only r2; with one real root r, only c3 < 0 gives a crossing.
+// The decisions (which case, which root) are taken on FP64 quantities; the
+// chosen root is evaluated in FP32 and then polished by two FP64 Newton steps
+// on the cubic itself, so the result has FP64 accuracy without FP64
+// transcendentals. The coefficients are first scaled by a power of two
+// (exact) so that the largest has magnitude in [0.5, 1).
 __device__ bool first_maximiser(double c0, double c1, double c2, double c3, double* t_out) {
   const double s = fmax(fmax(fabs(c0), fabs(c1)), fmax(fabs(c2), fabs(c3)));
+  if (!(s > 0.0) || !isfinite(s)) return false;
+  // 2^-e with s = m 2^e, m in [0.5, 1): built from the exponent field of s
+  // (s is finite and positive; subnormal s are scaled twice)
+  double sc = 1.0;
+  double ss = s;
+  if (ss < 0x1p-1000) {
+    sc = 0x1p+1000;
+    ss *= sc;
+  }
+  const int ex = min(1000, ((__double2hiint(ss) >> 20) & 0x7ff) - 1022);
+  sc *= __hiloint2double((1023 - ex) << 20, 0);
+  c0 *= sc;
+  c1 *= sc;
+  c2 *= sc;
+  c3 *= sc;
   double t = -1.0;
-  if (fabs(c3) <= 1e-12 * s) {
+  if (fabs(c3) <= 1e-12) {
     // quadratic c2 t^2 + c1 t + c0 (or linear)
-    if (fabs(c2) <= 1e-12 * s) {
-      if (c1 < 0.0) t = -c0 / c1;
+    if (fabs(c2) <= 1e-12) {
+      if (c1 < 0.0) t = (double)(-(float)c0 / (float)c1);
     } else {
       const double disc = c1 * c1 - 4.0 * c2 * c0;
       if (disc >= 0.0) {
-        const double q = -0.5 * (c1 + copysign(sqrt(disc), c1));
-        const double ra = q / c2, rb = c0 / q;
-        const double lo = fmin(ra, rb), hi = fmax(ra, rb);
+        const float qf = -0.5f * ((float)c1 + copysignf(sqrtf((float)disc), (float)c1));
+        const float ra = qf / (float)c2, rb = (float)c0 / qf;
+        const float lo = fminf(ra, rb), hi = fmaxf(ra, rb);
         // c2 < 0: + between the roots, so + -> - at the larger root;
         // c2 > 0: + outside them, so + -> - at the smaller root
-        t = (c2 < 0.0) ? hi : lo;
+        t = (double)((c2 < 0.0) ? hi : lo);
         if (!(t > 0.0)) t = -1.0;
       }
     }
   } else {
-    const double r3 = 1.0 / c3;
+    const double r3 = recip_refined(c3);
     const double B = c2 * r3, C = c1 * r3, D = c0 * r3;
     const double B3 = B * (1.0 / 3.0);
-    const double p = C - B * B3;
-    const double q = (2.0 / 27.0) * B * B * B - B3 * C + D;
-    const double disc = 0.25 * q * q + (1.0 / 27.0) * p * p * p;
+    const double p = fma(-B, B3, C);
+    const double q = fma((2.0 / 27.0) * B * B, B, fma(-B3, C, D));
+    const double disc = fma(0.25 * q, q, (1.0 / 27.0) * p * p * p);
+    const float pf = (float)p, qf = (float)q, B3f = (float)B3;
     if (disc > 0.0) {
       if (c3 < 0.0) {
-        const double u = -copysign(cbrt(0.5 * fabs(q) + sqrt(disc)), q);
-        t = (u != 0.0 ? u - p / (3.0 * u) : 0.0) - B3;
+        const float u = -copysignf(cbrtf(0.5f * fabsf(qf) + sqrtf((float)disc)), qf);
+        t = (double)((u != 0.0f ? u - pf / (3.0f * u) : 0.0f) - B3f);
       }
     } else if (p < 0.0) {
       // roots m cos(phi - 2 pi k / 3) - B/3: k = 0 largest, k = 1 middle, k = 2 smallest
-      const double m = 2.0 * sqrt(-p * (1.0 / 3.0));
-      const double arg = fmin(1.0, fmax(-1.0, 3.0 * q / (p * m)));
-      const double phi = acos(arg) * (1.0 / 3.0);
-      const double two_pi_3 = 2.0943951023931954923084289221863;
+      const float m = 2.0f * sqrtf(-pf * (1.0f / 3.0f));
+      const float arg = fminf(1.0f, fmaxf(-1.0f, 3.0f * qf / (pf * m)));
+      const float phi = acosf(arg) * (1.0f / 3.0f);
+      const float two_pi_3 = 2.09439510239319549f;
       if (c3 < 0.0) {
-        const double r1 = m * cos(phi - 2.0 * two_pi_3) - B3;
-        t = r1 > 0.0 ? r1 : m * cos(phi) - B3;
+        // (the hardware cosine is accurate enough for a start the polish refines)
+        const float r1 = m * __cosf(phi - 2.0f * two_pi_3) - B3f;
+        t = (double)(r1 > 0.0f ? r1 : m * __cosf(phi) - B3f);
       } else {
-        t = m * cos(phi - two_pi_3) - B3;   // k = 1: middle root
+        t = (double)(m * __cosf(phi - two_pi_3) - B3f);   // k = 1: middle root
       }
     } else {
       t = -1.0;   // triple root: G'' vanishes there, so it is not a strict maximum
     }
-    if (t > 0.0) {  // one Newton polish on the original cubic
-      const double f = ((c3 * t + c2) * t + c1) * t + c0;
-      const double fp = (3.0 * c3 * t + 2.0 * c2) * t + c1;
-      if (fp != 0.0) {
-        const double tn = t - f / fp;
+  }
+  if (t > 0.0) {  // two Newton polishes on the cubic, slope inverted in FP32
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const double f = fma(fma(fma(c3, t, c2), t, c1), t, c0);
+      const double fp = fma(fma(3.0 * c3, t, 2.0 * c2), t, c1);
+      const float fpf = (float)fp;
+      if (fpf != 0.0f && isfinite(fpf)) {
+        const double tn = fma(-f, (double)(1.0f / fpf), t);
         if (tn > 0.0 && isfinite(tn)) t = tn;
       }
     }
@@ -293,12 +346,12 @@ __device__ void exp_se3(const double tw[6], double dR[9], double dT[3]) {
 
 // Gradient tail: sums (F, omega', v, pairs, candidates) -> F, metric
 // gradient, unit step direction in the centred frame.
-__device__ void finish_gradient(const SolveCfg* cfg, BlockCtx& b, const double sums[9]) {
-  const double s2 = cfg->sigma2;
+__device__ void finish_gradient(BlockCtx& b, const double sums[9]) {
+  const double s2 = b.tc.sigma2;
   const double v[3] = {sums[4], sums[5], sums[6]};
   double cxv[3];
-  cross3d(cfg->cX, v, cxv);
-  const double ka = s2 * b.inv_l2 / cfg->a2, kb = s2 * b.inv_l2 / cfg->b2;
+  cross3d(b.tc.cX, v, cxv);
+  const double ka = s2 * b.inv_l2 * b.tc.inv_a2, kb = s2 * b.inv_l2 * b.tc.inv_b2;
   double nrm2 = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -307,14 +360,29 @@ __device__ void finish_gradient(const SolveCfg* cfg, BlockCtx& b, const double s
   }
 #pragma unroll
   for (int a = 0; a < 6; ++a) nrm2 += b.xi[a] * b.xi[a];
-  const double nrm = sqrt(nrm2);
+  // |xi| and 1/|xi|: FP32 rsqrt refined by two FP64 Newton steps
+  // y <- y (1.5 - 0.5 x y^2) (relative error 1e-7 -> 1e-14 -> 1e-28)
+  double inv = 0.0, nrm = 0.0;
+  if (nrm2 > 0.0 && nrm2 < 1e300) {
+    inv = (double)rsqrtf((float)nrm2);
+    if (inv > 0.0 && isfinite(inv)) {
+      inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
+      inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
+      nrm = nrm2 * inv;
+    } else {
+      nrm = sqrt(nrm2);
+      inv = 1.0 / nrm;
+    }
+  } else if (nrm2 > 0.0) {
+    nrm = sqrt(nrm2);
+    inv = 1.0 / nrm;
+  }
   b.xi_norm = nrm;
   b.F = s2 * sums[0];
   b.nnz_grad = (unsigned long long)sums[7];
   b.cand_grad = (unsigned long long)sums[8];
   double wxc[3];
-  cross3d(b.xi, cfg->cX, wxc);
-  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  cross3d(b.xi, b.tc.cX, wxc);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     b.om[a] = (float)(b.xi[a] * inv);
@@ -323,9 +391,10 @@ __device__ void finish_gradient(const SolveCfg* cfg, BlockCtx& b, const double s
 }
 
 // Step tail: S0..S4, step length, pose update, stop test.
-__device__ void finish_step(const SolveCfg* cfg, BlockCtx& b, const double sums[7]) {
+__device__ void finish_step(BlockCtx& b, const double sums[7]) {
+  const TailConst& tc = b.tc;
   const double nxi = b.xi_norm;
-  double pw = cfg->sigma2;
+  double pw = tc.sigma2;
 #pragma unroll
   for (int m = 0; m < 5; ++m) {  // the sums were taken along xi / |xi|
     b.S[m] = sums[m] * pw;
@@ -333,7 +402,7 @@ __device__ void finish_step(const SolveCfg* cfg, BlockCtx& b, const double sums[
   }
   b.nnz_total += b.nnz_grad + (unsigned long long)sums[5];
   b.cand_total += b.cand_grad + (unsigned long long)sums[6];
-  if (cfg->mode == kModeEval) {
+  if (tc.mode == kModeEval) {
     b.done = 1;
     return;
   }
@@ -343,7 +412,7 @@ __device__ void finish_step(const SolveCfg* cfg, BlockCtx& b, const double sums[
     b.no_ascent += 1;
   } else {
     bool ok;
-    if (cfg->step_order == 2) {
+    if (tc.step_order == 2) {
       ok = b.S[2] < 0.0;
       t = ok ? -b.S[1] / (2.0 * b.S[2]) : 0.0;
     } else {
@@ -372,70 +441,95 @@ __device__ void finish_step(const SolveCfg* cfg, BlockCtx& b, const double sums[
   b.t = t;
   b.t_prev = t;
   b.have_t_prev = 1;
-  const bool conv = (b.ell == cfg->ell_floor) &&
-                    (fabs(t) * nxi < cfg->eps_pose || nxi < cfg->eps_grad);
+  const bool conv = (b.ell == tc.ell_floor) &&
+                    (fabs(t) * nxi < tc.eps_pose || nxi < tc.eps_grad);
   b.k += 1;
-  if (conv || b.k >= cfg->max_iters) {
+  if (conv || b.k >= tc.max_iters) {
     b.done = 1;
     b.converged = conv ? 1 : 0;
   }
 }
 
-// Bounded grid barrier. Every block calls it the same number of times; the
-// cooperative launch keeps all blocks resident. A block that polls for
-// kSpinLimit rounds raises kStatusTimeout and every block then leaves the
-// solve loop at its next barrier.
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Release the barrier of generation g (thread 0 of the last block to arrive).
+__device__ __forceinline__ void barrier_release(SolveState* st, unsigned g) {
+  atomicExch(&st->bar_count, 0u);
+  __threadfence();
+  st_release_u32(&st->bar_gen, g + 1);
+}
+
+// Wait for generation g to be released (thread 0). A block that polls
+// kSpinLimit times raises kStatusTimeout and returns false; its team then
+// leaves the solve loop when the other blocks' own waits run out at the next
+// barrier, which the timed-out block never reaches (an error path, bounded).
+__device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned g) {
+  unsigned spins = 0;
+  while (ld_acquire(&st->bar_gen) == g) {
+    if (++spins > kSpinLimit) {
+      atomicOr(&st->status, (int)kStatusTimeout);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// Bounded barrier of the team's nblk blocks. Every block calls it the same
+// number of times; all blocks are resident (cooperative launch).
 __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = 1;
     const unsigned g = gen;
     __threadfence();
     const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    int ok = 1;
     if (arrived == (unsigned)nblk - 1) {
-      atomicExch(&st->bar_count, 0u);
-      __threadfence();
-      atomicExch(&st->bar_gen, g + 1);
+      barrier_release(st, g);
     } else {
-      unsigned spins = 0;
-      while (ld_acquire(&st->bar_gen) == g) {
-        if (++spins > kSpinLimit) {
-          ok = 0;
-          atomicOr(&st->status, (int)kStatusTimeout);
-          break;
-        }
-        __nanosleep(64);
-      }
+      ok = barrier_wait(st, g) ? 1 : 0;
     }
     __threadfence();
     gen = g + 1;
-    if (ld_acquire((const unsigned*)&st->status) & kStatusTimeout) ok = 0;
     *s_flag = ok;
   }
   __syncthreads();
   return *s_flag != 0;
 }
 
-// Fixed-order FP64 sum of all block partials. Warp w sums values w and w + 8:
-// lane l adds blocks l, l + 32, ... (all loads issued first, then a pairwise
-// tree), then a shuffle tree across lanes. Results land in out[] (shared).
-// Must be called by every thread of the block.
-__device__ void reduce_partials(const double* partials, int nvals, double* out, int nblk) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kMaxPerLane = 16;   // blocks per lane: up to 512 blocks
-  for (int i = warp; i < nvals; i += kWarps) {
-    double v[kMaxPerLane];
+// Fixed-order FP64 sum of the nblk (<= 2 * kThreads) block partials: thread t
+// loads blocks t and t + kThreads of every value at once (one L2 round trip),
+// then a shuffle tree per warp and the warps in order. Results land in out[]
+// (shared). Must be called by every thread of the block.
+template <class Smem>
+__device__ void reduce_partials(const double* partials, int nvals, double* out, int nblk,
+                                Smem& sm) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double v[kPartialStride];
 #pragma unroll
-    for (int q = 0; q < kMaxPerLane; ++q) {
-      const int b = lane + 32 * q;
-      v[q] = b < nblk ? __ldcg(&partials[(size_t)b * kPartialStride + i]) : 0.0;
+  for (int i = 0; i < kPartialStride; ++i) {
+    double a = 0.0, c = 0.0;
+    if (i < nvals) {
+      if (t < nblk) a = __ldcg(&partials[(size_t)t * kPartialStride + i]);
+      if (t + kThreads < nblk) c = __ldcg(&partials[(size_t)(t + kThreads) * kPartialStride + i]);
     }
+    v[i] = a + c;
+  }
 #pragma unroll
-    for (int w = kMaxPerLane / 2; w > 0; w >>= 1)
+  for (int i = 0; i < kPartialStride; ++i) {
+    if (i < nvals) {
+      const double w = warp_sum_d(v[i]);
+      if (lane == 0) sm.red_d[warp][i] = w;
+    }
+  }
+  __syncthreads();
+  if (t < nvals) {
+    double r = 0.0;
 #pragma unroll
-      for (int q = 0; q < w; ++q) v[q] += v[q + w];
-    const double s = warp_sum_d(v[0]);
-    if (lane == 0) out[i] = s;
+    for (int w = 0; w < kWarps; ++w) r += sm.red_d[w][t];
+    out[t] = r;
   }
   __syncthreads();
 }
@@ -454,40 +548,24 @@ __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const 
     sm.last = (arrived == (unsigned)nblk - 1) ? 1 : 0;
   }
   __syncthreads();
-  int ok = 1;
   const unsigned g = gen;
   if (sm.last) {
-    reduce_partials(partials, nvals, sm.sums, nblk);
+    reduce_partials(partials, nvals, sm.sums, nblk, sm);
     if (threadIdx.x < (unsigned)nvals) st->red_sums[threadIdx.x] = sm.sums[threadIdx.x];
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      atomicExch(&st->bar_count, 0u);
-      __threadfence();
-      atomicExch(&st->bar_gen, g + 1);
+      barrier_release(st, g);
+      sm.flag = 1;
     }
   } else {
     if (threadIdx.x == 0) {
-      unsigned spins = 0;
-      while (ld_acquire(&st->bar_gen) == g) {
-        if (++spins > kSpinLimit) {
-          ok = 0;
-          atomicOr(&st->status, (int)kStatusTimeout);
-          break;
-        }
-        __nanosleep(32);
-      }
+      sm.flag = barrier_wait(st, g) ? 1 : 0;
       __threadfence();
-      sm.flag = ok;
     }
     __syncthreads();
     if (threadIdx.x < (unsigned)nvals) sm.sums[threadIdx.x] = __ldcg(&st->red_sums[threadIdx.x]);
   }
   gen = g + 1;
-  if (threadIdx.x == 0) {
-    if (sm.last) sm.flag = 1;
-    if (ld_acquire((const unsigned*)&st->status) & kStatusTimeout) sm.flag = 0;
-  }
   __syncthreads();
   return sm.flag != 0;
 }
@@ -605,20 +683,25 @@ __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState*
   if (lane == 0) {
     cfg->cl_nseg[c] = min(nseg, kMaxSeg);
     cfg->cl_cand[c] = total;
+    cfg->cl_kept[c] = 0;
   }
 }
 
 // Work of cluster c under the current plan, in pair-test units: staging the
 // cluster costs cost_cluster, each 32-candidate chunk its cs4 pair tests per
 // lane (cluster size padded to a multiple of 4) plus cost_chunk of per-chunk
-// overhead. Chunk j starts at offset cost_cluster + j * (cs4 + cost_chunk).
+// overhead, plus (use_kept, once the plan's first gradient pass has counted
+// them) cost_kept per kept pair of the cluster, spread evenly over its chunks.
+// Chunk j starts at offset cost_cluster + j * k, k = the per-chunk cost.
 __device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const ClusterView& cv,
-                                                  int c, int* k_out) {
+                                                  int c, int* k_out, bool use_kept) {
   const int tc = __ldcg(&cfg->cl_cand[c]);
   const int cs4 = ((cv.cstart[c + 1] - cv.cstart[c]) + 3) & ~3;
-  const int k = cs4 + cfg->cost_chunk;
-  *k_out = k;
   const int nch = (tc + 31) >> 5;
+  int k = cs4 + cfg->cost_chunk;
+  if (use_kept && nch > 0)
+    k += (int)(cfg->cost_kept * (float)__ldcg(&cfg->cl_kept[c]) / (float)nch);
+  *k_out = k;
   return nch > 0 ? (long long)cfg->cost_cluster + (long long)nch * k : 0;
 }
 
@@ -631,6 +714,7 @@ struct SolveSmem {
   int xs[kWarps][kMaxSeg];
   int pf[kWarps][kMaxSeg + 1];
   float red[kWarps][10];
+  double red_d[kWarps][kPartialStride];
   long long scan[kThreads];
   long long bnd_base[2 * kWarps];   // work offset of the group holding each warp boundary
   int bnd_group[2 * kWarps];
@@ -638,6 +722,9 @@ struct SolveSmem {
   int flag, last;
   long long q_slot;                 // queue: claimed slot (-1: none left)
   int q_entry;                      //        entry that slot belongs to
+  short cache_n[kWarps];            // slots cached per warp (-1: streamed)
+  unsigned short cache_hdr[kWarps][32];
+  int cache_cl[kWarps][32];         // cluster of each cached cluster slot
   BlockCtx b;
 };
 
@@ -645,11 +732,11 @@ struct SolveSmem {
 // inside group `group` whose work starts at `base` (one warp). The chunk may
 // equal the cluster's chunk count, which means the next cluster's first chunk.
 __device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, long long base,
-                       long long s, int lane, int* c_out, int* j_out) {
+                       long long s, int lane, int* c_out, int* j_out, bool use_kept) {
   const int c = group * 32 + lane;
   long long w = 0;
   int kk = 4;
-  if (c < cv.ncl) w = cluster_work(cfg, cv, c, &kk);
+  if (c < cv.ncl) w = cluster_work(cfg, cv, c, &kk, use_kept);
   long long incl = w;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -717,7 +804,7 @@ __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid,
       c = cv.ncl;   // past the end: no chunk
       jj = 0;
     } else {
-      locate(cfg, cv, sm.bnd_group[q], sm.bnd_base[q], s, lane, &c, &jj);
+      locate(cfg, cv, sm.bnd_group[q], sm.bnd_base[q], s, lane, &c, &jj, sm.b.use_kept != 0);
     }
     if (lane == 0) {
       if (h == 0) {
@@ -732,24 +819,219 @@ __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid,
   __syncthreads();
 }
 
-// One warp's share of a pair pass; lane sums in acc, counts in nnz / cand.
+// Stage one cluster for a warp: lane j < cs holds the cluster's centred
+// source point p and its features; the transformed point z~' = R p + T (and,
+// for the step pass, the Taylor coefficient vectors of Eq. fourth) go to the
+// warp's shared-memory slots, read by every lane of the pair loop.
+template <bool STEP, int DP, int DPS, int NU>
+__device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, int lane, bool zv,
+                                              float4 p, const float pf[DPS]) {
+  const BlockCtx& b = sm.b;
+  float4 z = make_float4(kFar, kFar, kFar, 0.f);
+  if (zv) {
+    z.x = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
+    z.y = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
+    z.z = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
+  }
+  sm.z[warp][lane] = z;
+#pragma unroll
+  for (int d = 0; d < DP; ++d) sm.zf[warp][d][lane] = zv ? pf[d] : 0.f;
+  if (STEP) {
+    const float* om = b.om;
+    const float* vc = b.vc;
+    const float inv_l2 = b.inv_l2f;
+    const float zt[3] = {zv ? z.x : 0.f, zv ? z.y : 0.f, zv ? z.z : 0.f};
+    float u1[3], u2[3], u3[3], u4[3];
+    u1[0] = om[1] * zt[2] - om[2] * zt[1] + vc[0];
+    u1[1] = om[2] * zt[0] - om[0] * zt[2] + vc[1];
+    u1[2] = om[0] * zt[1] - om[1] * zt[0] + vc[2];
+    u2[0] = om[1] * u1[2] - om[2] * u1[1];
+    u2[1] = om[2] * u1[0] - om[0] * u1[2];
+    u2[2] = om[0] * u1[1] - om[1] * u1[0];
+    u3[0] = om[1] * u2[2] - om[2] * u2[1];
+    u3[1] = om[2] * u2[0] - om[0] * u2[2];
+    u3[2] = om[0] * u2[1] - om[1] * u2[0];
+    u4[0] = om[1] * u3[2] - om[2] * u3[1];
+    u4[1] = om[2] * u3[0] - om[0] * u3[2];
+    u4[2] = om[0] * u3[1] - om[1] * u3[0];
+    const float u11 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
+    const float u12 = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
+    const float u13 = u1[0] * u3[0] + u1[1] * u3[1] + u1[2] * u3[2];
+    const float u22 = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
+    // beta = e.U1; gamma = e.U2 - k2; delta = e.U3 - k3; eps = e.U4 - k4
+    const float c1 = inv_l2, c2 = 0.5f * inv_l2, c3 = inv_l2 * (1.0f / 6.0f),
+                c4 = inv_l2 * (1.0f / 24.0f);
+    sm.u[warp][0][lane] = make_float4(u1[0] * c1, u1[1] * c1, u1[2] * c1, 0.5f * u11 * inv_l2);
+    sm.u[warp][1 % NU][lane] = make_float4(u2[0] * c2, u2[1] * c2, u2[2] * c2, 0.5f * u12 * inv_l2);
+    sm.u[warp][2 % NU][lane] = make_float4(u3[0] * c3, u3[1] * c3, u3[2] * c3,
+                                           (u13 * (1.0f / 6.0f) + u22 * 0.125f) * inv_l2);
+    sm.u[warp][3 % NU][lane] = make_float4(u4[0] * c4, u4[1] * c4, u4[2] * c4, 0.f);
+  }
+}
+
+// One 32-candidate chunk against the staged cluster: lane = candidate x'
+// (xp, features xf; padding points lie beyond every cutoff), inner loop over
+// the cluster's cs4 points (cluster size rounded up to 4; padding slots lie
+// beyond the cutoff too). FP32 pair arithmetic, one ex2.approx per pair.
+// Points are taken four at a time: the four distance tests first, then, if
+// any lane of the warp keeps any of the four pairs (one vote, so the branch
+// is uniform), the four pair bodies without branches, a rejected pair
+// contributing exactly nothing (its weight is selected to zero and its step
+// terms are not added). The four bodies are independent, so their latencies
+// overlap.
 template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
-                          float acc[7], unsigned& nnz, unsigned& cand) {
+__device__ __forceinline__ void chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, float4 xp,
+                                            const float xf[DPS], int cs4, float rc2, float A,
+                                            float acc[7], unsigned& nnz) {
+  float W = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
+  for (int j0 = 0; j0 < cs4; j0 += 4) {
+    float ex[4], ey[4], ez[4], d2[4];
+    bool keep[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const float4 z = sm.z[warp][j0 + jj];
+      ex[jj] = xp.x - z.x;
+      ey[jj] = xp.y - z.y;
+      ez[jj] = xp.z - z.z;
+      d2[jj] = fmaf(ex[jj], ex[jj], fmaf(ey[jj], ey[jj], ez[jj] * ez[jj]));
+      keep[jj] = d2[jj] <= rc2;
+    }
+    if (!__any_sync(kFull, keep[0] | keep[1] | keep[2] | keep[3])) continue;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = j0 + jj;
+      float w;
+      if (MODE == kColorKernel) {
+        float qf = 0.f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+          const float df = xf[d] - sm.zf[warp][d][j];
+          qf = fmaf(df, df, qf);
+        }
+        w = ex2_approx(-fmaf(A, d2[jj], qf));
+      } else if (MODE == kColorDot) {
+        float cdot = 0.f;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) cdot = fmaf(xf[d], sm.zf[warp][d][j], cdot);
+        w = ex2_approx(-A * d2[jj]) * cdot;
+      } else {
+        w = ex2_approx(-A * d2[jj]);
+      }
+      w = keep[jj] ? w : 0.f;
+      nnz += keep[jj] ? 1u : 0u;
+      if (!STEP) {
+        // |e| <= 2 kFar is finite, so a zero weight adds exactly zero
+        W += w;
+        Ex = fmaf(w, ex[jj], Ex);
+        Ey = fmaf(w, ey[jj], Ey);
+        Ez = fmaf(w, ez[jj], Ez);
+      } else {
+        const float4 U1 = sm.u[warp][0][j], U2 = sm.u[warp][1 % NU][j];
+        const float4 U3 = sm.u[warp][2 % NU][j], U4 = sm.u[warp][3 % NU][j];
+        const float beta = fmaf(ex[jj], U1.x, fmaf(ey[jj], U1.y, ez[jj] * U1.z));
+        const float gam = fmaf(ex[jj], U2.x, fmaf(ey[jj], U2.y, fmaf(ez[jj], U2.z, -U1.w)));
+        const float del = fmaf(ex[jj], U3.x, fmaf(ey[jj], U3.y, fmaf(ez[jj], U3.z, -U2.w)));
+        const float eps = fmaf(ex[jj], U4.x, fmaf(ey[jj], U4.y, fmaf(ez[jj], U4.z, -U3.w)));
+        const float b2 = beta * beta;
+        const float g2 = fmaf(0.5f, b2, gam);
+        const float g3 = fmaf(beta, fmaf(b2, 1.0f / 6.0f, gam), del);
+        const float g4 = fmaf(b2 * b2, 1.0f / 24.0f,
+                              fmaf(0.5f * gam, b2 + gam, fmaf(beta, del, eps)));
+        // the polynomial of a far padding pair may overflow: select, not scale
+        acc[0] += w;
+        acc[1] = keep[jj] ? fmaf(w, beta, acc[1]) : acc[1];
+        acc[2] = keep[jj] ? fmaf(w, g2, acc[2]) : acc[2];
+        acc[3] = keep[jj] ? fmaf(w, g3, acc[3]) : acc[3];
+        acc[4] = keep[jj] ? fmaf(w, g4, acc[4]) : acc[4];
+      }
+    }
+  }
+  if (!STEP) {
+    // x' fixed per lane: sum_j w (z~'_j x e_ij) = x' x E_i
+    acc[0] += W;
+    acc[1] += xp.y * Ez - xp.z * Ey;
+    acc[2] += xp.z * Ex - xp.x * Ez;
+    acc[3] += xp.x * Ey - xp.y * Ex;
+    acc[4] += Ex;
+    acc[5] += Ey;
+    acc[6] += Ez;
+  }
+}
+
+// Segments of cluster c into the warp's shared arrays, and the segment that
+// holds candidate q0 (binary search over the candidate offsets).
+template <int DPS, int NU>
+__device__ __forceinline__ int load_segments(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
+                                             int lane, int c, int tc, int q0) {
+  const int nseg = __ldcg(&cfg->cl_nseg[c]);
+  for (int i = lane; i < nseg; i += 32) {
+    sm.xs[warp][i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
+    sm.pf[warp][i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
+  }
+  if (lane == 0) sm.pf[warp][nseg] = tc;
+  __syncwarp();
+  int lo = 0, hi = nseg;
+  if (q0 < tc) {
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (sm.pf[warp][mid] <= q0) lo = mid;
+      else hi = mid;
+    }
+  }
+  return lo;
+}
+
+// Candidate q of the staged cluster (padding beyond tc), advancing seg.
+template <int DP, int DPS, int NU>
+__device__ __forceinline__ float4 load_candidate(const GridView& g, SolveSmem<DPS, NU>& sm, int warp,
+                                                 int q, int tc, int& seg, float xf[DPS]) {
+  float4 xp = make_float4(-kFar, -kFar, -kFar, 0.f);
+#pragma unroll
+  for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
+  if (q < tc) {
+    while (sm.pf[warp][seg + 1] <= q) ++seg;
+    const int xi = sm.xs[warp][seg] + (q - sm.pf[warp][seg]);
+    xp = g.xyz[xi];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) xf[d] = g.feat[d * g.n_pad + xi];
+  }
+  return xp;
+}
+
+// Kept pairs of cluster c counted by this warp, added to the plan's
+// per-cluster totals (one atomic per warp and cluster).
+__device__ __forceinline__ void add_kept(const SolveCfg* cfg, int c, unsigned kept, int lane) {
+  unsigned k = kept;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) k += __shfl_down_sync(kFull, k, off);
+  if (lane == 0 && c >= 0 && k) atomicAdd(&cfg->cl_kept[c], (int)k);
+}
+
+// One warp's share of a pair pass, streamed from global memory (L2): lane
+// sums in acc, counts in nnz / cand.
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ void pass_stream(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
+                            float acc[7], unsigned& nnz, unsigned& cand) {
   const BlockCtx& b = sm.b;
   const GridView& g = cfg->grids[b.level];
   const ClusterView& cv = cfg->clusters[b.level];
   const float rc2 = b.rc2, A = b.A;
   int c = b.w_c0[warp], jc = b.w_j0[warp];
   const int c_end = b.w_c1[warp], j_end = b.w_j1[warp];
-  int loaded = -1, cs = 0, cs4 = 0, tc = 0, nch_c = 0, nseg = 0, seg = 0;
+  int loaded = -1, cs = 0, cs4 = 0, tc = 0, nch_c = 0, seg = 0;
   float4 xp_next = make_float4(-kFar, -kFar, -kFar, 0.f);
   float xf_next[DPS];
 #pragma unroll
   for (int d = 0; d < DPS; ++d) xf_next[d] = 0.f;
   bool have_next = false;
+  const bool collect = !STEP && b.collect_kept;
+  unsigned nnz0 = nnz;
   for (;;) {
     if (c != loaded) {
+      if (collect) {
+        add_kept(cfg, loaded, nnz - nnz0, lane);
+        nnz0 = nnz;
+      }
       for (;;) {  // the next cluster that still has a chunk in this warp's range
         if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) return;
         tc = __ldcg(&cfg->cl_cand[c]);
@@ -762,69 +1044,20 @@ __device__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
       const int p0 = cv.cstart[c];
       cs = cv.cstart[c + 1] - p0;
       const bool zv = lane < cs;
-      float4 z = make_float4(kFar, kFar, kFar, 0.f);
-      if (zv) {
-        const float4 p = cfg->src.xyz[p0 + lane];
-        z.x = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
-        z.y = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
-        z.z = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
-      }
-      sm.z[warp][lane] = z;
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+      float pf[DPS];
 #pragma unroll
-      for (int d = 0; d < DP; ++d)
-        sm.zf[warp][d][lane] = zv ? cfg->src.feat[d * cfg->src.m_pad + p0 + lane] : 0.f;
-      if (STEP) {
-        const float* om = b.om;
-        const float* vc = b.vc;
-        const float inv_l2 = b.inv_l2f;
-        const float zt[3] = {zv ? z.x : 0.f, zv ? z.y : 0.f, zv ? z.z : 0.f};
-        float u1[3], u2[3], u3[3], u4[3];
-        u1[0] = om[1] * zt[2] - om[2] * zt[1] + vc[0];
-        u1[1] = om[2] * zt[0] - om[0] * zt[2] + vc[1];
-        u1[2] = om[0] * zt[1] - om[1] * zt[0] + vc[2];
-        u2[0] = om[1] * u1[2] - om[2] * u1[1];
-        u2[1] = om[2] * u1[0] - om[0] * u1[2];
-        u2[2] = om[0] * u1[1] - om[1] * u1[0];
-        u3[0] = om[1] * u2[2] - om[2] * u2[1];
-        u3[1] = om[2] * u2[0] - om[0] * u2[2];
-        u3[2] = om[0] * u2[1] - om[1] * u2[0];
-        u4[0] = om[1] * u3[2] - om[2] * u3[1];
-        u4[1] = om[2] * u3[0] - om[0] * u3[2];
-        u4[2] = om[0] * u3[1] - om[1] * u3[0];
-        const float u11 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
-        const float u12 = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
-        const float u13 = u1[0] * u3[0] + u1[1] * u3[1] + u1[2] * u3[2];
-        const float u22 = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
-        // beta = e.U1; gamma = e.U2 - k2; delta = e.U3 - k3; eps = e.U4 - k4
-        const float c1 = inv_l2, c2 = 0.5f * inv_l2, c3 = inv_l2 * (1.0f / 6.0f),
-                    c4 = inv_l2 * (1.0f / 24.0f);
-        sm.u[warp][0][lane] = make_float4(u1[0] * c1, u1[1] * c1, u1[2] * c1, 0.5f * u11 * inv_l2);
-        sm.u[warp][1 % NU][lane] = make_float4(u2[0] * c2, u2[1] * c2, u2[2] * c2, 0.5f * u12 * inv_l2);
-        sm.u[warp][2 % NU][lane] = make_float4(u3[0] * c3, u3[1] * c3, u3[2] * c3,
-                                               (u13 * (1.0f / 6.0f) + u22 * 0.125f) * inv_l2);
-        sm.u[warp][3 % NU][lane] = make_float4(u4[0] * c4, u4[1] * c4, u4[2] * c4, 0.f);
+      for (int d = 0; d < DPS; ++d) pf[d] = 0.f;
+      if (zv) {
+        p = cfg->src.xyz[p0 + lane];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) pf[d] = cfg->src.feat[d * cfg->src.m_pad + p0 + lane];
       }
-      nseg = __ldcg(&cfg->cl_nseg[c]);
-      for (int i = lane; i < nseg; i += 32) {
-        sm.xs[warp][i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
-        sm.pf[warp][i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
-      }
-      if (lane == 0) sm.pf[warp][nseg] = tc;
+      stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, zv, p, pf);
       cs4 = (cs + 3) & ~3;
       loaded = c;
       have_next = false;
-      __syncwarp();
-      // this lane's segment for chunk jc (binary search once per cluster)
-      const int q0 = jc * 32 + lane;
-      int lo = 0, hi = nseg;
-      if (q0 < tc) {
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (sm.pf[warp][mid] <= q0) lo = mid;
-          else hi = mid;
-        }
-      }
-      seg = lo;
+      seg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, jc * 32 + lane);
     }
     // candidate of chunk jc (prefetched during the previous chunk of the same
     // cluster) and the prefetch of chunk jc + 1
@@ -835,98 +1068,18 @@ __device__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
 #pragma unroll
       for (int d = 0; d < DPS; ++d) xf[d] = xf_next[d];
     } else {
-      xp = make_float4(-kFar, -kFar, -kFar, 0.f);
-#pragma unroll
-      for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
-      const int q = jc * 32 + lane;
-      if (q < tc) {
-        while (sm.pf[warp][seg + 1] <= q) ++seg;
-        const int xi = sm.xs[warp][seg] + (q - sm.pf[warp][seg]);
-        xp = g.xyz[xi];
-#pragma unroll
-        for (int d = 0; d < DP; ++d) xf[d] = g.feat[d * g.n_pad + xi];
-      }
+      xp = load_candidate<DP, DPS, NU>(g, sm, warp, jc * 32 + lane, tc, seg, xf);
     }
     if (jc * 32 + lane < tc) cand += (unsigned)cs;
     const bool last_of_range = (c == c_end && jc + 1 >= j_end);
     have_next = (jc + 1 < nch_c) && !last_of_range;
-    if (have_next) {
-      xp_next = make_float4(-kFar, -kFar, -kFar, 0.f);
-#pragma unroll
-      for (int d = 0; d < DPS; ++d) xf_next[d] = 0.f;
-      const int q = (jc + 1) * 32 + lane;
-      if (q < tc) {
-        while (sm.pf[warp][seg + 1] <= q) ++seg;
-        const int xi = sm.xs[warp][seg] + (q - sm.pf[warp][seg]);
-        xp_next = g.xyz[xi];
-#pragma unroll
-        for (int d = 0; d < DP; ++d) xf_next[d] = g.feat[d * g.n_pad + xi];
-      }
+    if (have_next) xp_next = load_candidate<DP, DPS, NU>(g, sm, warp, (jc + 1) * 32 + lane, tc, seg,
+                                                         xf_next);
+    chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, cs4, rc2, A, acc, nnz);
+    if (last_of_range) {
+      if (collect) add_kept(cfg, loaded, nnz - nnz0, lane);
+      return;
     }
-    float W = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
-    for (int j0 = 0; j0 < cs4; j0 += 4) {
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int j = j0 + jj;
-        const float4 z = sm.z[warp][j];
-        const float ex = xp.x - z.x, ey = xp.y - z.y, ez = xp.z - z.z;
-        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-        if (d2 <= rc2) {
-          float w;
-          if (MODE == kColorKernel) {
-            float qf = 0.f;
-#pragma unroll
-            for (int d = 0; d < DP; ++d) {
-              const float df = xf[d] - sm.zf[warp][d][j];
-              qf = fmaf(df, df, qf);
-            }
-            w = ex2_approx(-fmaf(A, d2, qf));
-          } else if (MODE == kColorDot) {
-            float cdot = 0.f;
-#pragma unroll
-            for (int d = 0; d < DP; ++d) cdot = fmaf(xf[d], sm.zf[warp][d][j], cdot);
-            w = ex2_approx(-A * d2) * cdot;
-          } else {
-            w = ex2_approx(-A * d2);
-          }
-          ++nnz;
-          if (!STEP) {
-            W += w;
-            Ex = fmaf(w, ex, Ex);
-            Ey = fmaf(w, ey, Ey);
-            Ez = fmaf(w, ez, Ez);
-          } else {
-            const float4 U1 = sm.u[warp][0][j], U2 = sm.u[warp][1 % NU][j];
-            const float4 U3 = sm.u[warp][2 % NU][j], U4 = sm.u[warp][3 % NU][j];
-            const float beta = fmaf(ex, U1.x, fmaf(ey, U1.y, ez * U1.z));
-            const float gam = fmaf(ex, U2.x, fmaf(ey, U2.y, fmaf(ez, U2.z, -U1.w)));
-            const float del = fmaf(ex, U3.x, fmaf(ey, U3.y, fmaf(ez, U3.z, -U2.w)));
-            const float eps = fmaf(ex, U4.x, fmaf(ey, U4.y, fmaf(ez, U4.z, -U3.w)));
-            const float b2 = beta * beta;
-            const float g2 = fmaf(0.5f, b2, gam);
-            const float g3 = fmaf(beta, fmaf(b2, 1.0f / 6.0f, gam), del);
-            const float g4 = fmaf(b2 * b2, 1.0f / 24.0f,
-                                  fmaf(0.5f * gam, b2 + gam, fmaf(beta, del, eps)));
-            acc[0] += w;
-            acc[1] = fmaf(w, beta, acc[1]);
-            acc[2] = fmaf(w, g2, acc[2]);
-            acc[3] = fmaf(w, g3, acc[3]);
-            acc[4] = fmaf(w, g4, acc[4]);
-          }
-        }
-      }
-    }
-    if (!STEP) {
-      // x' fixed per lane: sum_j w (z~'_j x e_ij) = x' x E_i
-      acc[0] += W;
-      acc[1] += xp.y * Ez - xp.z * Ey;
-      acc[2] += xp.z * Ex - xp.x * Ez;
-      acc[3] += xp.x * Ey - xp.y * Ex;
-      acc[4] += Ex;
-      acc[5] += Ey;
-      acc[6] += Ez;
-    }
-    if (last_of_range) return;
     if (++jc >= nch_c) {
       ++c;
       jc = 0;
@@ -934,16 +1087,150 @@ __device__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
   }
 }
 
+// Shared-memory cache of a warp's share of the plan. A slot holds 32 points
+// (float4 xyz, then DP feature planes of 32 floats): either the raw centred
+// source points of a cluster (header kSlotCluster | cluster size) or the 32
+// candidates of a chunk (header = number of valid candidates; the rest are
+// padding points beyond every cutoff). Filled once per plan when the warp's
+// whole share fits, so that the passes of every iteration that reuses the
+// plan (at the lengthscale floor, most of the solve) read no global memory.
+constexpr int kCacheSlots = 32;                 // header capacity per warp
+constexpr unsigned short kSlotCluster = 0x8000;
+
+template <int DP>
+__device__ __forceinline__ constexpr int slot_floats() {
+  return 32 * (4 + DP);
+}
+
+template <int DP, int DPS, int NU>
+__device__ void fill_cache(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
+                           float* cache, int slots) {
+  const BlockCtx& b = sm.b;
+  const GridView& g = cfg->grids[b.level];
+  const ClusterView& cv = cfg->clusters[b.level];
+  const int c0 = b.w_c0[warp], j0 = b.w_j0[warp];
+  const int c_end = b.w_c1[warp], j_end = b.w_j1[warp];
+  // count the slots the share needs
+  int need = 0;
+  {
+    int c = c0, jc = j0;
+    for (;;) {
+      if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) break;
+      const int nch = (__ldcg(&cfg->cl_cand[c]) + 31) >> 5;
+      if (jc < nch) {
+        const int jl = (c == c_end) ? min(nch, j_end) : nch;
+        need += 1 + (jl - jc);
+      }
+      ++c;
+      jc = 0;
+    }
+  }
+  if (need > min(slots, kCacheSlots)) {
+    if (lane == 0) sm.cache_n[warp] = -1;
+    __syncwarp();
+    return;
+  }
+  float* base = cache + (size_t)warp * slots * slot_floats<DP>();
+  int n = 0;
+  int c = c0, jc = j0;
+  for (;;) {
+    if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) break;
+    const int tc = __ldcg(&cfg->cl_cand[c]);
+    const int nch = (tc + 31) >> 5;
+    if (jc < nch) {
+      const int jl = (c == c_end) ? min(nch, j_end) : nch;
+      const int p0 = cv.cstart[c];
+      const int cs = cv.cstart[c + 1] - p0;
+      float* sl = base + (size_t)n * slot_floats<DP>();
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lane < cs) p = cfg->src.xyz[p0 + lane];
+      reinterpret_cast<float4*>(sl)[lane] = p;
+#pragma unroll
+      for (int d = 0; d < DP; ++d)
+        sl[128 + d * 32 + lane] = lane < cs ? cfg->src.feat[d * cfg->src.m_pad + p0 + lane] : 0.f;
+      if (lane == 0) {
+        sm.cache_hdr[warp][n] = (unsigned short)(kSlotCluster | cs);
+        sm.cache_cl[warp][n] = c;
+      }
+      ++n;
+      int seg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, jc * 32 + lane);
+      for (int k = jc; k < jl; ++k) {
+        float xf[DPS];
+        const float4 xp = load_candidate<DP, DPS, NU>(g, sm, warp, k * 32 + lane, tc, seg, xf);
+        float* sk = base + (size_t)n * slot_floats<DP>();
+        reinterpret_cast<float4*>(sk)[lane] = xp;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) sk[128 + d * 32 + lane] = xf[d];
+        if (lane == 0) sm.cache_hdr[warp][n] = (unsigned short)min(32, tc - k * 32);
+        ++n;
+      }
+      __syncwarp();   // the segment arrays are reused by the next cluster
+    }
+    ++c;
+    jc = 0;
+  }
+  if (lane == 0) sm.cache_n[warp] = (short)n;
+  __syncwarp();
+}
+
+// The same share as pass_stream, from the warp's cache.
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
+                            const float* cache, int slots, float acc[7], unsigned& nnz,
+                            unsigned& cand) {
+  const float rc2 = sm.b.rc2, A = sm.b.A;
+  const bool collect = !STEP && sm.b.collect_kept;
+  const float* base = cache + (size_t)warp * slots * slot_floats<DP>();
+  const int n = sm.cache_n[warp];
+  int cs = 0, cs4 = 0, cur = -1;
+  unsigned nnz0 = nnz;
+  for (int s = 0; s < n; ++s) {
+    const unsigned h = sm.cache_hdr[warp][s];
+    const float* sl = base + (size_t)s * slot_floats<DP>();
+    const float4 p = reinterpret_cast<const float4*>(sl)[lane];
+    float f[DPS];
+#pragma unroll
+    for (int d = 0; d < DPS; ++d) f[d] = d < DP ? sl[128 + d * 32 + lane] : 0.f;
+    if (h & kSlotCluster) {
+      if (collect) {
+        add_kept(cfg, cur, nnz - nnz0, lane);
+        cur = sm.cache_cl[warp][s];
+        nnz0 = nnz;
+      }
+      __syncwarp();   // every lane is done with the previous cluster
+      cs = (int)(h & 0xff);
+      stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, lane < cs, p, f);
+      cs4 = (cs + 3) & ~3;
+      __syncwarp();
+    } else {
+      if (lane < (int)h) cand += (unsigned)cs;
+      chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, p, f, cs4, rc2, A, acc, nnz);
+    }
+  }
+  if (collect) add_kept(cfg, cur, nnz - nnz0, lane);
+}
+
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ __forceinline__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
+                                          int lane, const float* cache, int slots, float acc[7],
+                                          unsigned& nnz, unsigned& cand) {
+  if (sm.cache_n[warp] >= 0)
+    pass_cached<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots, acc, nnz, cand);
+  else
+    pass_stream<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, acc, nnz, cand);
+}
+
 // One pass over the block's warps, then the block partial (fixed order).
 template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials, int rank) {
+__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials, int rank,
+                         const float* cache, int slots) {
   constexpr int NACC = STEP ? 5 : 7;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float acc[7];
 #pragma unroll
   for (int i = 0; i < 7; ++i) acc[i] = 0.f;
   unsigned nnz = 0, cand = 0;
-  pass_warp<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, acc, nnz, cand);
+  pass_warp<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots, acc, nnz, cand);
   __syncwarp();
 #pragma unroll
   for (int i = 0; i < NACC; ++i) {
@@ -1000,7 +1287,8 @@ __device__ void publish(SolveState* st, const BlockCtx& b) {
 template <int DP, int MODE, int DPS, int NU>
 __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
                            double* __restrict__ partials, IterRecord* __restrict__ records,
-                           Team team, SolveSmem<DPS, NU>& sm, bool join) {
+                           Team team, SolveSmem<DPS, NU>& sm, bool join, float* cache,
+                           int slots) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned gen = 0;
   double* part_g = partials;
@@ -1010,6 +1298,21 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
 
   if (tid == 0) {
     BlockCtx& b = sm.b;
+    TailConst& tc = b.tc;
+    for (int a = 0; a < 3; ++a) {
+      tc.cX[a] = cfg->cX[a];
+      tc.cZ[a] = cfg->cZ[a];
+    }
+    tc.sigma2 = cfg->sigma2;
+    tc.inv_a2 = 1.0 / cfg->a2;
+    tc.inv_b2 = 1.0 / cfg->b2;
+    tc.ell_floor = cfg->ell_floor;
+    tc.eps_pose = cfg->eps_pose;
+    tc.eps_grad = cfg->eps_grad;
+    tc.src_radius = cfg->src_radius;
+    tc.mode = cfg->mode;
+    tc.step_order = cfg->step_order;
+    tc.max_iters = cfg->max_iters;
     for (int i = 0; i < 16; ++i) b.P[i] = st->P0[i];
     b.k = 0;
     b.level = 0;
@@ -1017,6 +1320,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     b.need_plan = 1;
     b.done = cfg->max_iters <= 0 ? 1 : 0;
     b.converged = b.fallback = b.no_ascent = b.have_t_prev = 0;
+    b.use_kept = b.collect_kept = b.rebalance = 0;
     b.t = b.t_prev = 0.0;
     b.nnz_total = b.cand_total = b.nnz_grad = b.cand_grad = 0;
     b.F = b.xi_norm = 0.0;
@@ -1024,7 +1328,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     for (int i = 0; i < 5; ++i) b.S[i] = 0.0;
     b.r_plan = 0.0;
     b.plan_ell = 0.0;
-    if (!b.done) begin_iteration(cfg, b);
+    if (!b.done) begin_iteration(cfg->iters[0], b);
   }
   __syncthreads();
   if (join && !team_join(st, team.size, sm)) {
@@ -1038,35 +1342,51 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     const bool stamp = records != nullptr && team.rank == 0 && tid == 0;
     if (stamp) t0 = globaltimer();
     const int replan = sm.b.need_plan;
-    if (replan) {
+    // a new plan, or the one rebalance of a plan that is being reused: its
+    // work split redone with the kept pairs its first gradient pass counted
+    const int rebalance = !replan && sm.b.rebalance;
+    if (replan || rebalance) {
       const ClusterView& cv = cfg->clusters[sm.b.level];
-      for (long long c = gw; c < cv.ncl; c += NW) plan_cluster(cfg, sm.b, st, (int)c, lane);
-      if (!grid_sync(st, gen, &sm.flag, team.size)) break;
+      if (replan) {
+        for (long long c = gw; c < cv.ncl; c += NW) plan_cluster(cfg, sm.b, st, (int)c, lane);
+        if (!grid_sync(st, gen, &sm.flag, team.size)) break;
+      }
+      if (tid == 0) sm.b.use_kept = rebalance;
+      __syncthreads();
       const int ng = (cv.ncl + 31) / 32;
       for (long long gi = gw; gi < ng; gi += NW) {
         const int c = (int)gi * 32 + lane;
         int kk;
-        long long w = c < cv.ncl ? cluster_work(cfg, cv, c, &kk) : 0;
+        long long w = c < cv.ncl ? cluster_work(cfg, cv, c, &kk, rebalance != 0) : 0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(kFull, w, off);
         if (lane == 0) cfg->group_agg[gi] = w;
       }
       if (!grid_sync(st, gen, &sm.flag, team.size)) break;
       split_work<DPS, NU>(cfg, sm, tid, team);
-      if (tid == 0) sm.b.need_plan = 0;
+      fill_cache<DP, DPS, NU>(cfg, sm, warp, lane, cache, slots);
+      if (tid == 0) {
+        sm.b.need_plan = 0;
+        sm.b.collect_kept = replan && cfg->cost_kept > 0.f;
+        sm.b.rebalance = sm.b.collect_kept;
+        if (rebalance) sm.b.rebalance = 0;
+      }
       __syncthreads();
     }
     if (stamp) t1 = globaltimer();
     // ---- gradient pass ----
-    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g, team.rank);
+    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g, team.rank, cache, slots);
     if (stamp) tg1 = globaltimer();
     if (!grid_sync_reduce(st, gen, sm, part_g, 9, team.size)) break;
     if (stamp) tg2 = globaltimer();
-    if (tid == 0) finish_gradient(cfg, sm.b, sm.sums);
+    if (tid == 0) {
+      sm.b.collect_kept = 0;
+      finish_gradient(sm.b, sm.sums);
+    }
     __syncthreads();
     if (stamp) t2 = globaltimer();
     // ---- step pass ----
-    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s, team.rank);
+    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s, team.rank, cache, slots);
     if (stamp) ts1 = globaltimer();
     if (!grid_sync_reduce(st, gen, sm, part_s, 7, team.size)) break;
     if (stamp) ts2 = globaltimer();
@@ -1074,9 +1394,11 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
       if (tid == 0) {
         BlockCtx& b = sm.b;
         const int k = b.k;
+        // the next iteration's constants, loaded now and used after the tail
+        const IterConst ic_next = cfg->iters[min(k + 1, b.tc.max_iters - 1)];
         const unsigned long long pairs_before = b.nnz_total;
-        finish_step(cfg, b, sm.sums);
-        if (stamp && k < cfg->max_iters) {
+        finish_step(b, sm.sums);
+        if (stamp && k < b.tc.max_iters) {
           IterRecord& r = records[k];
           r.ell = b.ell;
           r.t_plan_ns = (float)(t1 - t0);
@@ -1091,7 +1413,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
           r.step_pairs = (long long)(b.nnz_total - pairs_before - b.nnz_grad);
           r.grad_candidates = (long long)b.cand_grad;
         }
-        if (!b.done) begin_iteration(cfg, b);
+        if (!b.done) begin_iteration(ic_next, b);
       }
     }
     __syncthreads();
@@ -1108,12 +1430,13 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
 template <int DP, int MODE>
 __global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
 solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
-             double* __restrict__ partials, IterRecord* __restrict__ records) {
+             double* __restrict__ partials, IterRecord* __restrict__ records, int cache_slots) {
   constexpr int DPS = DP > 0 ? DP : 1;
   constexpr int NU = 4;
   __shared__ SolveSmem<DPS, NU> sm;
+  extern __shared__ float4 dyn_smem[];
   solve_pair<DP, MODE, DPS, NU>(cfg, st, partials, records, Team{(int)blockIdx.x, (int)gridDim.x},
-                                sm, false);
+                                sm, false, reinterpret_cast<float*>(dyn_smem), cache_slots);
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
@@ -1209,10 +1532,11 @@ template <int DP, int MODE>
 __global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
 queue_kernel(const QueueEntry* __restrict__ entries, const QueueCtl* __restrict__ ctl,
              unsigned long long* __restrict__ head, int* __restrict__ kstatus,
-             unsigned long long idle_limit_ns) {
+             unsigned long long idle_limit_ns, int cache_slots) {
   constexpr int DPS = DP > 0 ? DP : 1;
   constexpr int NU = 4;
   __shared__ SolveSmem<DPS, NU> sm;
+  extern __shared__ float4 dyn_smem[];
   for (;;) {
     if (threadIdx.x == 0) {
       long long slot;
@@ -1225,7 +1549,8 @@ queue_kernel(const QueueEntry* __restrict__ entries, const QueueCtl* __restrict_
     if (sm.q_slot < 0) break;
     const QueueEntry en = load_entry(entries + sm.q_entry);
     const Team team{(int)(sm.q_slot - en.slot0), en.team};
-    solve_pair<DP, MODE, DPS, NU>(en.cfg, en.st, en.partials, nullptr, team, sm, true);
+    solve_pair<DP, MODE, DPS, NU>(en.cfg, en.st, en.partials, nullptr, team, sm, true,
+                                  reinterpret_cast<float*>(dyn_smem), cache_slots);
     if (threadIdx.x == 0) {
       __threadfence();
       const unsigned left = atomicAdd(&en.st->leave_count, 1u);
@@ -1238,28 +1563,74 @@ queue_kernel(const QueueEntry* __restrict__ entries, const QueueCtl* __restrict_
   }
 }
 
+// Dynamic shared memory of the plan cache: what CVO_SOLVE_MIN_BLOCKS blocks
+// per SM leave of the SM's shared memory after their static shared memory,
+// in whole warp shares of slots (set once per kernel instantiation).
+struct CacheCfg {
+  int bytes = 0, slots = 0;
+  cudaError_t err = cudaSuccess;
+};
+
+template <int DP, int MODE>
+const CacheCfg& cache_cfg() {
+  static const CacheCfg cfg = [] {
+    CacheCfg c;
+    int dev = 0, smem_sm = 0, reserved = 0;
+    cudaFuncAttributes fa{};
+    c.err = cudaGetDevice(&dev);
+    if (c.err == cudaSuccess)
+      c.err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (c.err == cudaSuccess)
+      c.err = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (c.err == cudaSuccess) c.err = cudaFuncGetAttributes(&fa, solve_kernel<DP, MODE>);
+    if (c.err != cudaSuccess) return c;
+    const int slot_bytes = 4 * 32 * (4 + DP);
+    const int avail = smem_sm / CVO_SOLVE_MIN_BLOCKS - reserved - (int)fa.sharedSizeBytes;
+    c.slots = std::max(0, std::min(kCacheSlots, avail / (kWarps * slot_bytes)));
+    c.bytes = c.slots * kWarps * slot_bytes;
+    if (c.bytes > 0) {
+      c.err = cudaFuncSetAttribute(solve_kernel<DP, MODE>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, c.bytes);
+      if (c.err == cudaSuccess)
+        c.err = cudaFuncSetAttribute(queue_kernel<DP, MODE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, c.bytes);
+    }
+    return c;
+  }();
+  return cfg;
+}
+
 template <int DP, int MODE>
 cudaError_t launch_solve_t(int nblocks, const SolveCfg* cfg, SolveState* st, double* partials,
                            IterRecord* records, cudaStream_t s) {
-  void* args[] = {(void*)&cfg, (void*)&st, (void*)&partials, (void*)&records};
+  const CacheCfg& cc = cache_cfg<DP, MODE>();
+  if (cc.err != cudaSuccess) return cc.err;
+  int slots = cc.slots;
+  void* args[] = {(void*)&cfg, (void*)&st, (void*)&partials, (void*)&records, (void*)&slots};
   return cudaLaunchCooperativeKernel((const void*)solve_kernel<DP, MODE>, dim3(nblocks),
-                                     dim3(kThreads), args, 0, s);
+                                     dim3(kThreads), args, (size_t)cc.bytes, s);
 }
 
 template <int DP, int MODE>
 cudaError_t launch_queue_t(int nblocks, const QueueEntry* entries, const QueueCtl* ctl,
                            unsigned long long* head, int* kstatus, unsigned long long idle_ns,
                            cudaStream_t s) {
-  void* args[] = {(void*)&entries, (void*)&ctl, (void*)&head, (void*)&kstatus, (void*)&idle_ns};
+  const CacheCfg& cc = cache_cfg<DP, MODE>();
+  if (cc.err != cudaSuccess) return cc.err;
+  int slots = cc.slots;
+  void* args[] = {(void*)&entries, (void*)&ctl,     (void*)&head,
+                  (void*)&kstatus, (void*)&idle_ns, (void*)&slots};
   return cudaLaunchCooperativeKernel((const void*)queue_kernel<DP, MODE>, dim3(nblocks),
-                                     dim3(kThreads), args, 0, s);
+                                     dim3(kThreads), args, (size_t)cc.bytes, s);
 }
 
 template <int DP, int MODE>
 int blocks_per_sm_t() {
+  const CacheCfg& cc = cache_cfg<DP, MODE>();
+  if (cc.err != cudaSuccess) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<DP, MODE>, kThreads, 0) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<DP, MODE>, kThreads,
+                                                    (size_t)cc.bytes) != cudaSuccess)
     return 0;
   return n;
 }

@@ -66,6 +66,7 @@ struct Plan {
   int* seg_pref = nullptr;
   int* cl_nseg = nullptr;
   int* cl_cand = nullptr;
+  int* cl_kept = nullptr;
   long long* group_agg = nullptr;
   int cap_iters = 0, cap_ncl = 0;
   int nblocks = 0;

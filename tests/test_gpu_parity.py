@@ -261,6 +261,12 @@ def test_align_table1_schedule_and_second_order(cvo):
     _align_parity(cvo, d, {"step_order": 2, "max_iters": 60})
 
 
+def test_align_with_kept_pair_rebalance(cvo):
+    # the rebalanced work split only reorders the FP64 sums over blocks
+    d = synth.planes_pair(2500, 2300, seed=synth.seed_for(1, 11))
+    _align_parity(cvo, d, {"cost_kept": 2.0})
+
+
 def test_align_paper_color_dot(cvo):
     d = synth.planes_pair(1500, 1500, seed=synth.seed_for(1, 10))
     _align_parity(cvo, d, {"color_mode": cvo.CVO_COLOR_DOT, "color_scale": 1e-5, "max_iters": 60})
