@@ -82,6 +82,9 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="instead of the benchmark line, print the dense precision sweep "
+                         "(100k points: FP64 reductions vs FP32 reductions vs BF16 features)")
     return ap.parse_args()
 
 
@@ -489,6 +492,59 @@ def bench_serving(cvo, seconds):
     return out
 
 
+def precision_sweep():
+    """Dense pair (N = M = 100,000 room points): error of F, gradient and step
+    sums at a fixed pose against the FP64 oracle, and of the final pose of a
+    full solve against the oracle's own full solve (exhaustive FP64, about two
+    minutes on the host cores), for FP32 pairs + FP64 reductions (the
+    default), FP32 reductions and BF16 features."""
+    import oracle
+    import paper_1904_02266_gb300 as cvo
+    from paper_1904_02266_gb300 import build as cvo_build
+    cvo_build.build()
+    d = synth.room_pair(n_points=100000, seed=synth.seed_for(4), mode="valid")
+    P, ell = np.eye(4), 0.05
+    modes = {"fp32_pairs_fp64_reductions": {}, "fp32_reductions": {"reduce_fp32": 1},
+             "bf16_features": {"feat_bf16": 1}}
+    out = {"workload": "room frames, 95% of valid pixels subsampled to 100,000 points each",
+           "pose": "identity", "ell": ell, "modes": {}}
+    prm = None
+    ref = grad_ref = None
+    P_default = None
+    prm = oracle.Params()
+    t0 = time.time()
+    ref = oracle.pair_sums(d["X"], d["FX"], d["Z"], d["FZ"], P, ell, prm)
+    grad_ref = oracle.gradient(ref, prm)
+    out["oracle_eval_s"] = time.time() - t0
+    t0 = time.time()
+    ref_align = oracle.align(d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4), prm)
+    out["oracle_align_s"] = time.time() - t0
+    out["oracle_iters"] = ref_align["iters"]
+    for name, kw in modes.items():
+        with cvo.Context(device=0, **kw) as ctx:
+            ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+            g = ctx.eval(ht, hs, P, ell)
+            s_ref = oracle.pair_sums(d["X"], d["FX"], d["Z"], d["FZ"], P, ell, prm,
+                                     xi=g["grad6"])["S"]
+            ctx.align(ht, hs)
+            t0 = time.perf_counter()
+            Pf, st = ctx.align(ht, hs)
+            dt = time.perf_counter() - t0
+            if P_default is None:
+                P_default = Pf
+            out["modes"][name] = {
+                "F_rel_err": abs(g["F"] - ref["F"]) / abs(ref["F"]),
+                "grad_rel_err": float(np.linalg.norm(g["grad6"] - grad_ref) / np.linalg.norm(grad_ref)),
+                "S_rel_err": float(np.max(np.abs(np.asarray(g["S"]) - s_ref) /
+                                          np.maximum(np.abs(s_ref), 1e-300))),
+                "kept_pairs_diff": int(g["nnz"] - ref["nnz"]),
+                "solve_ms": dt * 1e3, "iters": st["iters"],
+                "pose_vs_oracle": list(synth_pose_err(Pf, ref_align["P"])),
+                "pose_vs_default": list(synth_pose_err(Pf, P_default)),
+                "pose_vs_truth": list(synth_pose_err(Pf, d["P_gt"]))}
+    print(json.dumps({"precision_sweep": out}), flush=True)
+
+
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
     summary was taken on the current kernel source (else None)."""
@@ -520,6 +576,10 @@ def synth_pose_err(P, Pref):
 def main():
     args = parse_args()
     world, rank, local = dist_env()
+    if args.precision_sweep:
+        if rank == 0:
+            precision_sweep()
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

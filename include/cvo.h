@@ -83,6 +83,13 @@ typedef struct {
     double eps_grad;    /* ... or when |xi| < eps_grad there; 5e-5 (Table 1) */
     int step_order;     /* 4: first maximiser of the quartic Taylor model (Eq. fourth); 2: quadratic */
     int feat_dim;       /* feature dimension D in [0, CVO_MAX_FEAT]; 5. 0 forces COLOR_NONE */
+    int feat_bf16;      /* 1: store the (pre-scaled) features as BF16, rounded to nearest even,
+                           and widen them to FP32 in the pair arithmetic (half the feature bytes;
+                           the label product then carries BF16 rounding); 0: FP32. Not used by
+                           cvo_eval_gradient_static. 0 */
+    int reduce_fp32;    /* precision study only: 1 sums the block partials and the cross-block
+                           reduction in FP32 instead of FP64 (pair arithmetic and tail unchanged);
+                           0 */
     double cell_factor; /* cell edge of the target grid as a multiple of the cutoff radius, in
                            [0.5, 8]; 0.7. Performance only: the cutoff test is exact. */
     /* performance tuning (results do not depend on these): */
@@ -270,7 +277,18 @@ typedef struct {
                               frames can run while solves do; >= 1; 8 */
     int max_inflight;      /* requests admitted to the device at once, in [1, 65536]; 1024 */
     double linger_ms;      /* the serving kernel stays resident this long without work; 0.5 */
+    double idle_limit_ms;  /* device-side bound on the serving kernel's wait for new requests:
+                              past it the kernel exits by itself (counted in idle_exits) even if
+                              the host never told it to; > 0; 10000 */
 } cvo_serve_params;
+
+typedef struct {
+    int64_t submitted;        /* requests accepted by cvo_submit */
+    int64_t completed;        /* requests finished (successfully or not) */
+    int64_t failed;           /* requests finished with a status other than CVO_OK */
+    int64_t kernels_launched; /* serving kernels started (one per busy period) */
+    int64_t idle_exits;       /* serving kernels that left on their own idle bound */
+} cvo_serve_stats;
 
 /* Fill *p with the defaults listed in cvo_serve_params. */
 void cvo_serve_params_default(cvo_serve_params* p);
@@ -306,6 +324,10 @@ int cvo_poll(cvo_ctx* ctx, uint64_t ticket, cvo_result* out, int* done);
 /* Finish every queued and running request, then stop the loop and free its
  * device resources. Results stay available to cvo_poll. */
 int cvo_serve_stop(cvo_ctx* ctx);
+
+/* Counters of the context's request loop since the context was created
+ * (zeros if it never ran). */
+int cvo_serve_get_stats(cvo_ctx* ctx, cvo_serve_stats* out);
 
 /* Gradient pass for callers that must not allocate device memory during the
  * call: a program whose device memory is all owned by its own pool or fixed

@@ -40,7 +40,7 @@ EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
            "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile", "cvo_stream",
            "cvo_batch_create", "cvo_batch_run", "cvo_batch_get_info", "cvo_batch_destroy",
            "cvo_serve_params_default", "cvo_serve_start", "cvo_submit", "cvo_poll",
-           "cvo_serve_stop",
+           "cvo_serve_stop", "cvo_serve_get_stats",
            "cvo_eval_gradient_static", "cvo_strerror", "cvo_last_error")
 
 
@@ -63,6 +63,7 @@ class cvo_params(ctypes.Structure):
                 ("b2", ctypes.c_double), ("max_iters", ctypes.c_int),
                 ("eps_pose", ctypes.c_double), ("eps_grad", ctypes.c_double),
                 ("step_order", ctypes.c_int), ("feat_dim", ctypes.c_int),
+                ("feat_bf16", ctypes.c_int), ("reduce_fp32", ctypes.c_int),
                 ("cell_factor", ctypes.c_double), ("cluster_factor", ctypes.c_double),
                 ("cost_chunk", ctypes.c_int), ("cost_cluster", ctypes.c_int),
                 ("cost_kept", ctypes.c_double), ("team_factor", ctypes.c_double)]
@@ -110,7 +111,13 @@ class cvo_result(ctypes.Structure):
 
 class cvo_serve_params(ctypes.Structure):
     _fields_ = [("reserve_blocks", ctypes.c_int), ("max_inflight", ctypes.c_int),
-                ("linger_ms", ctypes.c_double)]
+                ("linger_ms", ctypes.c_double), ("idle_limit_ms", ctypes.c_double)]
+
+
+class cvo_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("kernels_launched", ctypes.c_int64),
+                ("idle_exits", ctypes.c_int64)]
 
 
 _lib = None
@@ -165,6 +172,7 @@ def load_library(path: str = LIB_PATH):
         lib.cvo_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(cvo_result),
                                  ctypes.POINTER(ctypes.c_int)]
         lib.cvo_serve_stop.argtypes = [vp]
+        lib.cvo_serve_get_stats.argtypes = [vp, ctypes.POINTER(cvo_serve_stats)]
         lib.cvo_stream.argtypes = [vp]
         lib.cvo_stream.restype = ctypes.c_void_p
         lib.cvo_strerror.argtypes = [ctypes.c_int]
@@ -174,7 +182,7 @@ def load_library(path: str = LIB_PATH):
         for name in ("cvo_create", "cvo_destroy", "cvo_set_cloud", "cvo_release_cloud",
                      "cvo_eval", "cvo_align", "cvo_batch_create", "cvo_batch_run",
                      "cvo_batch_get_info", "cvo_batch_destroy", "cvo_serve_start",
-                     "cvo_submit", "cvo_poll", "cvo_serve_stop"):
+                     "cvo_submit", "cvo_poll", "cvo_serve_stop", "cvo_serve_get_stats"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -385,6 +393,12 @@ def cvo_serve_stop(ctx) -> None:
     _check(ctx, load_library().cvo_serve_stop(ctx))
 
 
+def cvo_serve_get_stats(ctx) -> dict:
+    st = cvo_serve_stats()
+    _check(ctx, load_library().cvo_serve_get_stats(ctx, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in cvo_serve_stats._fields_}
+
+
 def cvo_eval_gradient_static(x, fx, z, fz, params: cvo_params, P, ell: float, out,
                              stream=None) -> None:
     """Allocation-free gradient pass on device tensors (torch CUDA float32, or
@@ -493,6 +507,9 @@ class Context:
 
     def serve_stop(self) -> None:
         cvo_serve_stop(self.ctx)
+
+    def serve_stats(self) -> dict:
+        return cvo_serve_get_stats(self.ctx)
 
     @property
     def stream(self) -> int:

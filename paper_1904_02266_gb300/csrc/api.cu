@@ -58,6 +58,13 @@ int padded_dim(const cvo_params& p) {
   return 8;
 }
 
+// Mode the kernels are instantiated for: the label product, with kFeatBf16
+// when the feature planes hold BF16 values.
+int kernel_mode(const cvo_params& p) {
+  if (p.color_mode == CVO_COLOR_NONE || p.feat_dim == 0) return kColorNone;
+  return p.color_mode | (p.feat_bf16 ? kFeatBf16 : 0);
+}
+
 // Feature pre-scale: for the appearance kernel, sqrt(log2(e) / (2 ell_c^2)) so
 // that |f'_i - g'_j|^2 is the base-2 exponent; for the dot product, sqrt(s).
 float feature_scale(const cvo_params& p) {
@@ -151,7 +158,7 @@ int ensure_grid(cvo_ctx* ctx, Cloud* c, double h_req, int* index_out) {
   const int n = (int)c->n;
   int rc = dev_alloc(ctx, (void**)&g.xyz, sizeof(float4) * c->n_pad, &g.bytes);
   if (rc == CVO_OK && c->dp > 0)
-    rc = dev_alloc(ctx, (void**)&g.feat, sizeof(float) * c->dp * (size_t)c->n_pad, &g.bytes);
+    rc = dev_alloc(ctx, (void**)&g.feat, (size_t)c->fbytes * c->dp * c->n_pad, &g.bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&g.cell_start, sizeof(int) * (ncells + 1), &g.bytes);
   if (rc != CVO_OK) {
     free_grid(ctx, g);
@@ -160,7 +167,8 @@ int ensure_grid(cvo_ctx* ctx, Cloud* c, double h_req, int* index_out) {
   const float hf = (float)h;
   // built from the Morton-ordered copy: the stable cell sort keeps each cell's
   // points in Morton order, so consecutive candidates are spatially compact
-  cudaError_t e = build_grid(c->zs, c->zf, n, c->dp, c->n_pad, nx, ny, nz, c->lo[0], c->lo[1],
+  cudaError_t e = build_grid(c->zs, c->zf, n, c->dp, c->n_pad, c->fbytes == 2, nx, ny, nz,
+                             c->lo[0], c->lo[1],
                              c->lo[2], hf, g.xyz, g.feat, g.cell_start, ctx->pool, ctx->stream);
   if (e != cudaSuccess) {
     free_grid(ctx, g);
@@ -324,7 +332,7 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
     cfg.clusters[l].ncl = s->clusters[ki[l]].ncl;
     ncl_max = std::max(ncl_max, s->clusters[ki[l]].ncl);
   }
-  const int per_sm = solve_blocks_per_sm(s->dp, prm.color_mode);
+  const int per_sm = solve_blocks_per_sm(s->dp, kernel_mode(prm));
   if (per_sm <= 0) return fail(ctx, CVO_ERR_CUDA, "solve kernel cannot be resident");
   const int nblocks = std::min(per_sm * ctx->sms, 512);   // the tail reduction covers 512
   rc = reserve_plan(ctx, p, (int)ells.size(), ncl_max, nblocks);
@@ -368,6 +376,7 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   cfg.eps_grad = prm.eps_grad;
   cfg.max_iters = mode == kModeEval ? 1 : prm.max_iters;
   cfg.step_order = prm.step_order;
+  cfg.reduce_fp32 = prm.reduce_fp32;
   cfg.mode = mode;
   // pageable sources: the copies complete before the calls return
   CK(cudaMemcpyAsync(p->d_iters, ic.data(), sizeof(IterConst) * ic.size(), cudaMemcpyHostToDevice,
@@ -376,7 +385,7 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   p->h_cfg = cfg;
   p->n_iters = (int)ells.size();
   p->dp = s->dp;
-  p->color_mode = prm.color_mode;
+  p->color_mode = kernel_mode(prm);
   return CVO_OK;
 }
 
@@ -443,6 +452,7 @@ int create_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, b
   c->n_pad = (int)((n + 31) / 32 * 32);
   c->D = D;
   c->dp = padded_dim(ctx->prm);
+  c->fbytes = (c->dp > 0 && ctx->prm.feat_bf16) ? 2 : 4;
   float *raw_xyz = nullptr, *raw_feat = nullptr;
   int rc = CVO_OK;
   auto cleanup = [&](int code) {
@@ -497,14 +507,15 @@ int create_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, b
   rc = dev_alloc(ctx, (void**)&c->xyz, sizeof(float4) * c->n_pad, &c->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&c->zs, sizeof(float4) * c->n_pad, &c->bytes);
   if (rc == CVO_OK && c->dp > 0)
-    rc = dev_alloc(ctx, (void**)&c->feat, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
+    rc = dev_alloc(ctx, (void**)&c->feat, (size_t)c->fbytes * c->dp * c->n_pad, &c->bytes);
   if (rc == CVO_OK && c->dp > 0)
-    rc = dev_alloc(ctx, (void**)&c->zf, sizeof(float) * c->dp * (size_t)c->n_pad, &c->bytes);
+    rc = dev_alloc(ctx, (void**)&c->zf, (size_t)c->fbytes * c->dp * c->n_pad, &c->bytes);
   if (rc != CVO_OK) return cleanup(rc);
   e = pack_cloud(raw_xyz, raw_feat, (int)n, D, c->dp, c->n_pad, c->c[0], c->c[1], c->c[2],
-                 feature_scale(ctx->prm), c->xyz, c->feat, ctx->stream);
+                 feature_scale(ctx->prm), c->fbytes == 2, c->xyz, c->feat, ctx->stream);
   if (e == cudaSuccess)
-    e = morton_order(c->xyz, c->feat, (int)n, c->dp, c->n_pad, c->mf, c->zs, c->zf, ctx->pool,
+    e = morton_order(c->xyz, c->feat, (int)n, c->dp, c->n_pad, c->fbytes == 2, c->mf, c->zs, c->zf,
+                     ctx->pool,
                      ctx->stream);
   if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
   if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
@@ -597,7 +608,8 @@ int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cv
                   p.cluster_factor > 0.0 && p.cluster_factor <= 8.0 && p.cost_chunk >= 0 &&
                   p.cost_chunk <= 4096 && p.cost_cluster >= 0 && p.cost_cluster <= 65536 &&
                   p.team_factor > 0.0 && p.team_factor <= 1024.0 && p.cost_kept >= 0.0 &&
-                  p.cost_kept <= 1024.0;
+                  p.cost_kept <= 1024.0 && (p.feat_bf16 == 0 || p.feat_bf16 == 1) &&
+                  (p.reduce_fp32 == 0 || p.reduce_fp32 == 1);
   if (!ok) return CVO_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -918,7 +930,7 @@ int cvo_batch_create(cvo_ctx* ctx, int n, const int32_t* targets, const int32_t*
   }
   CK(cudaSetDevice(ctx->device));
   const Cloud* s0 = get_cloud(ctx, sources[0]);
-  const int per_sm = solve_blocks_per_sm(s0->dp, ctx->prm.color_mode);
+  const int per_sm = solve_blocks_per_sm(s0->dp, kernel_mode(ctx->prm));
   if (per_sm <= 0) return fail(ctx, CVO_ERR_CUDA, "solve kernel cannot be resident");
   const int nblocks = std::min(per_sm * ctx->sms, 512);
   if (team_sizes)
@@ -929,7 +941,7 @@ int cvo_batch_create(cvo_ctx* ctx, int n, const int32_t* targets, const int32_t*
   b->n = n;
   b->nblocks = nblocks;
   b->dp = s0->dp;
-  b->color_mode = ctx->prm.color_mode;
+  b->color_mode = kernel_mode(ctx->prm);
   b->plans.assign(n, nullptr);
   b->tgt.assign(targets, targets + n);
   b->src.assign(sources, sources + n);

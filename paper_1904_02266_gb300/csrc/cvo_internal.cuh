@@ -25,6 +25,10 @@ constexpr int kMaxSeg = 64;               // cell-row segments per cluster
 constexpr int kMortonBits = 10;           // Morton quantisation per axis
 
 enum : int { kColorNone = 0, kColorKernel = 1, kColorDot = 2 };
+// Kernel mode = label product | kFeatBf16 when feature planes hold BF16 values.
+constexpr int kFeatBf16 = 4;
+__host__ __device__ constexpr int color_of(int mode) { return mode & 3; }
+__host__ __device__ constexpr bool bf16_of(int mode) { return (mode & kFeatBf16) != 0; }
 enum : int { kModeAlign = 0, kModeEval = 1 };
 enum : int { kStatusSegOverflow = 1, kStatusTimeout = 2 };   // bits of SolveState::status
 enum : int { kStatusIdleTimeout = 4 };   // queue kernel: a block gave up waiting for entries
@@ -33,7 +37,8 @@ enum : int { kStatusIdleTimeout = 4 };   // queue kernel: a block gave up waitin
 // only cells within the cutoff radius of a source point are visited).
 struct GridView {
   const float4* xyz;       // n points sorted by cell (x fastest), centred; w unused
-  const float* feat;       // dp planes of n_pad floats, same order, pre-scaled
+  const float* feat;       // dp planes of n_pad values (FP32, or BF16 in bf16 mode), same order,
+                           // pre-scaled
   const int* cell_start;   // ncells + 1 offsets into xyz
   int n, n_pad;
   int nx, ny, nz;
@@ -50,7 +55,7 @@ struct ClusterView {
 
 struct SourceView {
   const float4* xyz;       // m points, Morton order, centred
-  const float* feat;       // dp planes of m_pad floats, pre-scaled
+  const float* feat;       // dp planes of m_pad values (FP32 or BF16), pre-scaled
   int m, m_pad;
 };
 
@@ -85,7 +90,7 @@ struct SolveCfg {
   double sigma2, a2, b2;
   double ell_floor, eps_pose, eps_grad;
   int max_iters, step_order, mode;
-  int pad0;
+  int reduce_fp32;         // precision study: block and cross-block sums in FP32
 };
 
 // Mutable state of one solve (device memory). The host writes the input
@@ -171,10 +176,12 @@ struct CloudStats {
 cudaError_t cloud_stats(const float* xyz, const float* feat, int n, int D,
                         CloudStats* d_out, cudaMemPool_t pool, cudaStream_t s);
 
-// Centre, pack (float4 xyz) and pre-scale features into dp SoA planes.
+// Centre, pack (float4 xyz) and pre-scale features into dp SoA planes of FP32
+// values, or of BF16 values (round to nearest even of the scaled FP32 value)
+// when bf16.
 cudaError_t pack_cloud(const float* xyz, const float* feat, int n, int D, int dp, int n_pad,
-                       double cx, double cy, double cz, float feat_scale,
-                       float4* out_xyz, float* out_feat, cudaStream_t s);
+                       double cx, double cy, double cz, float feat_scale, bool bf16,
+                       float4* out_xyz, void* out_feat, cudaStream_t s);
 
 // Morton quantisation shared by the source ordering and its clusters.
 struct MortonFrame {
@@ -185,8 +192,8 @@ struct MortonFrame {
 MortonFrame morton_frame(const float lo[3], const float hi[3]);
 
 // Reorder a packed cloud along a Morton curve of its bounding box.
-cudaError_t morton_order(const float4* xyz, const float* feat, int n, int dp, int n_pad,
-                         const MortonFrame& mf, float4* out_xyz, float* out_feat,
+cudaError_t morton_order(const float4* xyz, const void* feat, int n, int dp, int n_pad,
+                         bool bf16, const MortonFrame& mf, float4* out_xyz, void* out_feat,
                          cudaMemPool_t pool, cudaStream_t s);
 
 // Cut a Morton-ordered cloud into clusters: runs sharing the Morton prefix of
@@ -196,9 +203,9 @@ cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, floa
                            int* cstart, int* d_ncl, cudaStream_t s);
 
 // Build a cell list of edge h over a packed cloud.
-cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int n_pad,
+cudaError_t build_grid(const float4* xyz, const void* feat, int n, int dp, int n_pad, bool bf16,
                        int nx, int ny, int nz, float ox, float oy, float oz, float h,
-                       float4* out_xyz, float* out_feat, int* cell_start, cudaMemPool_t pool,
+                       float4* out_xyz, void* out_feat, int* cell_start, cudaMemPool_t pool,
                        cudaStream_t s);
 
 // ---- pair_kernels.cu -------------------------------------------------------
@@ -207,6 +214,7 @@ cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int 
 // kPartialStride doubles; records (may be NULL) one entry per iteration.
 cudaError_t launch_solve(int dp, int color_mode, int nblocks, const SolveCfg* cfg, SolveState* st,
                          double* partials, IterRecord* records, cudaStream_t s);
+// color_mode below is the kernel mode: the label product | kFeatBf16.
 // Many pairs in one cooperative launch of nblocks blocks (queue_kernel):
 // blocks claim slots through *head (zeroed before the launch) until the queue
 // is drained and ctl->stop is set, or until they have waited idle_limit_ns for

@@ -8,6 +8,7 @@
 // instead of O(N M). Every ordering here is produced by a stable sort, so a
 // cloud always packs to the same layout and pair sums are reproducible bit
 // for bit.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,6 +17,8 @@
 namespace cvo {
 
 namespace {
+
+inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
@@ -192,10 +195,22 @@ __global__ void stats_final_kernel(const double* __restrict__ psum, const float*
   *out = r;
 }
 
+template <typename T>
+__device__ __forceinline__ T to_feat(float v);
+template <>
+__device__ __forceinline__ float to_feat<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_feat<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+template <typename T>
 __global__ void pack_kernel(const float* __restrict__ xyz, const float* __restrict__ feat, int n,
                             int D, int dp, int n_pad, double cx, double cy, double cz,
                             float feat_scale, float4* __restrict__ out_xyz,
-                            float* __restrict__ out_feat) {
+                            T* __restrict__ out_feat) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
   if (i < n) {
@@ -203,10 +218,11 @@ __global__ void pack_kernel(const float* __restrict__ xyz, const float* __restri
     out_xyz[i] = make_float4((float)((double)x - cx), (float)((double)y - cy),
                              (float)((double)z - cz), 0.0f);
     for (int d = 0; d < dp; ++d)
-      out_feat[(int64_t)d * n_pad + i] = d < D ? feat[(int64_t)D * i + d] * feat_scale : 0.0f;
+      out_feat[(int64_t)d * n_pad + i] =
+          to_feat<T>(d < D ? feat[(int64_t)D * i + d] * feat_scale : 0.0f);
   } else {
     out_xyz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int d = 0; d < dp; ++d) out_feat[(int64_t)d * n_pad + i] = 0.0f;
+    for (int d = 0; d < dp; ++d) out_feat[(int64_t)d * n_pad + i] = to_feat<T>(0.0f);
   }
 }
 
@@ -308,9 +324,10 @@ __global__ void cell_keys_kernel(const float4* __restrict__ xyz, int n, int nx, 
   vals[i] = (uint32_t)i;
 }
 
-__global__ void gather_kernel(const float4* __restrict__ xyz, const float* __restrict__ feat,
+template <typename T>
+__global__ void gather_kernel(const float4* __restrict__ xyz, const T* __restrict__ feat,
                               const uint32_t* __restrict__ perm, int n, int dp, int n_pad,
-                              float4* __restrict__ out_xyz, float* __restrict__ out_feat) {
+                              float4* __restrict__ out_xyz, T* __restrict__ out_feat) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pad) return;
   if (p < n) {
@@ -319,8 +336,21 @@ __global__ void gather_kernel(const float4* __restrict__ xyz, const float* __res
     for (int d = 0; d < dp; ++d) out_feat[(int64_t)d * n_pad + p] = feat[(int64_t)d * n_pad + s];
   } else {
     out_xyz[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int d = 0; d < dp; ++d) out_feat[(int64_t)d * n_pad + p] = 0.0f;
+    for (int d = 0; d < dp; ++d) out_feat[(int64_t)d * n_pad + p] = T();
   }
+}
+
+// Features are moved as raw 16- or 32-bit values.
+void launch_gather(const float4* xyz, const void* feat, const uint32_t* perm, int n, int dp,
+                   int n_pad, bool bf16, float4* out_xyz, void* out_feat, cudaStream_t s) {
+  if (bf16)
+    gather_kernel<uint16_t><<<blocks_for(n_pad, 256), 256, 0, s>>>(
+        xyz, static_cast<const uint16_t*>(feat), perm, n, dp, n_pad, out_xyz,
+        static_cast<uint16_t*>(out_feat));
+  else
+    gather_kernel<float><<<blocks_for(n_pad, 256), 256, 0, s>>>(
+        xyz, static_cast<const float*>(feat), perm, n, dp, n_pad, out_xyz,
+        static_cast<float*>(out_feat));
 }
 
 // cell_start[c] = first sorted position whose key is >= c (binary search).
@@ -337,7 +367,6 @@ __global__ void cell_start_kernel(const uint32_t* __restrict__ sorted_keys, int 
   cell_start[c] = lo;
 }
 
-inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
 }  // namespace
 
@@ -394,10 +423,15 @@ cudaError_t cloud_stats(const float* xyz, const float* feat, int n, int D, Cloud
 }
 
 cudaError_t pack_cloud(const float* xyz, const float* feat, int n, int D, int dp, int n_pad,
-                       double cx, double cy, double cz, float feat_scale, float4* out_xyz,
-                       float* out_feat, cudaStream_t s) {
-  pack_kernel<<<blocks_for(n_pad, 256), 256, 0, s>>>(xyz, feat, n, D, dp, n_pad, cx, cy, cz,
-                                                      feat_scale, out_xyz, out_feat);
+                       double cx, double cy, double cz, float feat_scale, bool bf16,
+                       float4* out_xyz, void* out_feat, cudaStream_t s) {
+  if (bf16)
+    pack_kernel<__nv_bfloat16><<<blocks_for(n_pad, 256), 256, 0, s>>>(
+        xyz, feat, n, D, dp, n_pad, cx, cy, cz, feat_scale, out_xyz,
+        static_cast<__nv_bfloat16*>(out_feat));
+  else
+    pack_kernel<float><<<blocks_for(n_pad, 256), 256, 0, s>>>(
+        xyz, feat, n, D, dp, n_pad, cx, cy, cz, feat_scale, out_xyz, static_cast<float*>(out_feat));
   return cudaGetLastError();
 }
 
@@ -410,8 +444,8 @@ MortonFrame morton_frame(const float lo[3], const float hi[3]) {
   return mf;
 }
 
-cudaError_t morton_order(const float4* xyz, const float* feat, int n, int dp, int n_pad,
-                         const MortonFrame& mf, float4* out_xyz, float* out_feat,
+cudaError_t morton_order(const float4* xyz, const void* feat, int n, int dp, int n_pad,
+                         bool bf16, const MortonFrame& mf, float4* out_xyz, void* out_feat,
                          cudaMemPool_t pool, cudaStream_t s) {
   const float* lo = mf.lo;
   const float scale = mf.scale;
@@ -425,8 +459,7 @@ cudaError_t morton_order(const float4* xyz, const float* feat, int n, int dp, in
   }
   if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, 30, pool, s);
   if (e == cudaSuccess) {
-    gather_kernel<<<blocks_for(n_pad, 256), 256, 0, s>>>(xyz, feat, vals, n, dp, n_pad, out_xyz,
-                                                         out_feat);
+    launch_gather(xyz, feat, vals, n, dp, n_pad, bf16, out_xyz, out_feat, s);
     e = cudaGetLastError();
   }
   if (keys) cudaFreeAsync(keys, s);
@@ -449,9 +482,10 @@ cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, floa
   return cudaGetLastError();
 }
 
-cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int n_pad, int nx,
-                       int ny, int nz, float ox, float oy, float oz, float h, float4* out_xyz,
-                       float* out_feat, int* cell_start, cudaMemPool_t pool, cudaStream_t s) {
+cudaError_t build_grid(const float4* xyz, const void* feat, int n, int dp, int n_pad, bool bf16,
+                       int nx, int ny, int nz, float ox, float oy, float oz, float h,
+                       float4* out_xyz, void* out_feat, int* cell_start, cudaMemPool_t pool,
+                       cudaStream_t s) {
   const int ncells = nx * ny * nz;
   int bits = 1;
   while (bits < 32 && (1u << bits) < (uint32_t)ncells) ++bits;
@@ -465,8 +499,7 @@ cudaError_t build_grid(const float4* xyz, const float* feat, int n, int dp, int 
   }
   if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, bits, pool, s);
   if (e == cudaSuccess) {
-    gather_kernel<<<blocks_for(n_pad, 256), 256, 0, s>>>(xyz, feat, vals, n, dp, n_pad, out_xyz,
-                                                         out_feat);
+    launch_gather(xyz, feat, vals, n, dp, n_pad, bf16, out_xyz, out_feat, s);
     cell_start_kernel<<<blocks_for(ncells + 1, 256), 256, 0, s>>>(keys, n, ncells, cell_start);
     e = cudaGetLastError();
   }

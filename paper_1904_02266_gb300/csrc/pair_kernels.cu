@@ -1,1685 +1,51 @@
-// The CVO hot path on sm_103a: the cutoff-truncated all-pairs kernel
-// reductions behind each gradient-ascent iteration, plus the FP64 tail, all in
-// one persistent cooperative kernel per solve.
-//
-//  gradient pass  F = sum c_ij k(x_i, z~_j)                         (Eq. scalar)
-//                 dF/domega = (1/ell^2) sum w_ij (z~_j x e_ij)      (Eq. 3_gradient,
-//                 dF/dv     = (1/ell^2) sum w_ij e_ij                left-update signs)
-//  step pass      S0..S4 = sum w_ij g^m_ij along xi                  (Eq. fourth)
-//  tail (FP64)    xi = metric gradient (Eq. metric), t* = first maximiser of the
-//                 quartic, P <- exp(t* xi) P (Eqs. newstep, step), lengthscale
-//                 schedule and the Table 1 convergence test.
-//
-// One iteration (every block runs the same sequence; phases are separated by
-// a grid barrier whose spin is bounded):
-//  plan        (only when needed) one warp per source cluster (an octree node
-//              of the source, at most 32 points): transform, bounding box, and
-//              the rows of target cells within the plan radius, stored as
-//              segments of the cell-sorted target.                     barrier
-//              pair-test totals of groups of 32 clusters.               barrier
-//              every block scans the group totals and places its own warps on
-//              an even split of the pair tests (no further barrier).
-//  gradient    each warp walks its share of 32-candidate chunks: one lane per
-//  pass        candidate target point (coalesced load into registers, next
-//              chunk prefetched) against the cluster's source points staged in
-//              shared memory (broadcast reads). FP32 pairs, one ex2.approx per
-//              kept pair, per-lane FP32 sums, fixed-order reductions.  barrier
-//  tail        every block reduces all block partials in FP64 in the same
-//              order and runs the same FP64 tail, so no broadcast is needed.
-//  step pass   as above along the unit direction.                      barrier
-//  tail        step length, exponential-map update, next iteration.
-// The plan is reused while it still covers the cutoff: it is built with a
-// radius 10% wider than the cutoff and rebuilt when the grid level changes,
-// when the pose has drifted by more than that margin (an FP64 bound over the
-// whole source cloud), or when it has become much wider than needed.
+// Dispatch of the solve and queue kernels by feature layout. The kernels are
+// in pair_kernels.cuh, instantiated per feature width in pair_kernels_d*.cu.
 #include <cuda_runtime.h>
-#include <stdint.h>
-
-#include <algorithm>
 
 #include "cvo_internal.cuh"
 
-// Resident blocks per SM the solve kernel is compiled for (register budget).
-#ifndef CVO_SOLVE_MIN_BLOCKS
-#define CVO_SOLVE_MIN_BLOCKS 2
-#endif
-
 namespace cvo {
 
-namespace {
-
-constexpr float kFar = 1.0e18f;   // coordinate of padding points: never within any cutoff
-constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned kSpinLimit = 1u << 22;   // barrier polls before giving up (~2 s)
-// a queued team waits for its last block to come free for at most this long
-constexpr unsigned long long kJoinLimitNs = 60ull * 1000 * 1000 * 1000;
-constexpr double kSkin = 0.10;              // plan radius margin (fraction of the cutoff)
-constexpr double kLoose = 1.25;             // replan when the plan radius exceeds this factor
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ int cell_floor(float v, float o, float inv_h, int n) {
-  float q = floorf((v - o) * inv_h);
-  q = fminf(fmaxf(q, -1.0f), (float)n);
-  return (int)q;
-}
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
-  return v;
-}
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
-  return v;
-}
-
-// ---------------------------------------------------------------------------
-// per-block iteration state (identical in every block of a team)
-// ---------------------------------------------------------------------------
-
-// The blocks that solve one pair together: the whole grid for a single
-// solve, a contiguous run of claimed slots for a queued one.
-struct Team {
-  int rank, size;
-};
-
-// Scalars of the solve configuration that the FP64 tail reads every
-// iteration, copied once per solve so that the tail issues no dependent
-// global loads.
-struct TailConst {
-  double cX[3], cZ[3];
-  double sigma2, inv_a2, inv_b2;
-  double ell_floor, eps_pose, eps_grad, src_radius;
-  int mode, step_order, max_iters;
-};
-
-struct BlockCtx {
-  TailConst tc;
-  double P[16];           // current pose
-  double Rp[9], Tp[3];    // centred pose at the last plan
-  double xi[6];
-  double xi_norm, F;
-  double S[5];
-  double t, t_prev;
-  double ell, inv_l2, r_plan, plan_ell;
-  int k, level, plan_level;
-  int need_plan, done, converged, fallback, no_ascent, have_t_prev;
-  int use_kept, collect_kept, rebalance;   // kept-pair weighting of the work split
-  unsigned long long nnz_total, cand_total, nnz_grad, cand_grad;
-  float R[9], T[3];       // FP32 centred pose: z~' = R z' + T
-  float om[3], vc[3];     // unit step direction (centred frame)
-  float A, rc2, rplan_f, inv_l2f;
-  int w_c0[kWarps], w_j0[kWarps], w_c1[kWarps], w_j1[kWarps];   // warp ranges
-};
-
-__device__ __forceinline__ void cross3d(const double a[3], const double b[3], double o[3]) {
-  o[0] = a[1] * b[2] - a[2] * b[1];
-  o[1] = a[2] * b[0] - a[0] * b[2];
-  o[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// Centred pose in FP64: R and T' = R cZ + T - cX.
-__device__ void centred_pose(const TailConst& tc, const double P[16], double R[9], double T[3]) {
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    double tr = P[4 * r + 3] - tc.cX[r];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      R[3 * r + c] = P[4 * r + c];
-      tr = fma(P[4 * r + c], tc.cZ[c], tr);
-    }
-    T[r] = tr;
-  }
-}
-
-// Iteration k's constants (ic = the host table's entry k), the FP32 pose, and
-// whether the traversal plan must be rebuilt.
-__device__ void begin_iteration(const IterConst& ic, BlockCtx& b) {
-  b.ell = ic.ell;
-  b.inv_l2 = ic.inv_l2;
-  b.A = ic.A;
-  b.rc2 = ic.rc2;
-  b.inv_l2f = (float)ic.inv_l2;
-  double R[9], T[3];
-  centred_pose(b.tc, b.P, R, T);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) b.R[i] = (float)R[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) b.T[i] = (float)T[i];
-  // is the current plan still a superset of the pairs within the cutoff?
-  const double need = (double)ic.rprune;   // 1.001 r_c
-  // reuse only at an unchanged lengthscale (the floor of the schedule): while
-  // ell shrinks a fresh, tighter plan costs less than the extra candidates
-  bool replan = b.need_plan || ic.level != b.plan_level || ic.ell != b.plan_ell;
-  if (!replan) {
-    double d2r[9], d2t[3];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) d2r[i] = (R[i] - b.Rp[i]) * (R[i] - b.Rp[i]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d2t[i] = (T[i] - b.Tp[i]) * (T[i] - b.Tp[i]);
-    // pairwise sums: short dependent chains (FP64 latency dominates the tail)
-    const double dr = ((d2r[0] + d2r[1]) + (d2r[2] + d2r[3])) +
-                      ((d2r[4] + d2r[5]) + (d2r[6] + d2r[7])) + d2r[8];
-    const double dt = (d2t[0] + d2t[1]) + d2t[2];
-    // |dR z + dT| <= |dR|_F |z| + |dT| for every source point, |z| <= r_src
-    const double drift = ((double)sqrtf((float)dr) * b.tc.src_radius + (double)sqrtf((float)dt)) *
-                             (1.0 + 1e-5) + 1e-6 * need;
-    replan = (need + drift > b.r_plan) || (b.r_plan > kLoose * (need + drift));
-  }
-  b.level = ic.level;
-  if (replan) {
-    b.need_plan = 1;
-    b.plan_level = ic.level;
-    b.plan_ell = ic.ell;
-    b.r_plan = need * (1.0 + kSkin);
-    b.rplan_f = (float)b.r_plan;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) b.Rp[i] = R[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) b.Tp[i] = T[i];
-  }
-}
-
-// FP64 reciprocal from the FP32 one and two Newton steps r <- r (2 - x r)
-// (each squares the relative error: 1e-7 -> 1e-14 -> 1e-28). Finite,
-// nonzero x within FP32 range.
-__device__ __forceinline__ double recip_refined(double x) {
-  double r = (double)(1.0f / (float)x);
-  r = r * fma(-x, r, 2.0);
-  r = r * fma(-x, r, 2.0);
-  return r;
-}
-
-// Smallest positive t at which G'(t) = c0 + c1 t + c2 t^2 + c3 t^3 changes sign
-// from + to - (the first local maximum of the quartic model, Sec. 4 "Step
-// size"), given c0 = S1 > 0. With three real roots r1 < r2 < r3 the sign
-// pattern of G' decides: for c3 < 0 the + -> - crossings are r1 and r3, for
-// c3 > 0 only r2; with one real root r, only c3 < 0 gives a crossing.
-// The decisions (which case, which root) are taken on FP64 quantities; the
-// chosen root is evaluated in FP32 and then polished by two FP64 Newton steps
-// on the cubic itself, so the result has FP64 accuracy without FP64
-// transcendentals. The coefficients are first scaled by a power of two
-// (exact) so that the largest has magnitude in [0.5, 1).
-__device__ bool first_maximiser(double c0, double c1, double c2, double c3, double* t_out) {
-  const double s = fmax(fmax(fabs(c0), fabs(c1)), fmax(fabs(c2), fabs(c3)));
-  if (!(s > 0.0) || !isfinite(s)) return false;
-  // 2^-e with s = m 2^e, m in [0.5, 1): built from the exponent field of s
-  // (s is finite and positive; subnormal s are scaled twice)
-  double sc = 1.0;
-  double ss = s;
-  if (ss < 0x1p-1000) {
-    sc = 0x1p+1000;
-    ss *= sc;
-  }
-  const int ex = min(1000, ((__double2hiint(ss) >> 20) & 0x7ff) - 1022);
-  sc *= __hiloint2double((1023 - ex) << 20, 0);
-  c0 *= sc;
-  c1 *= sc;
-  c2 *= sc;
-  c3 *= sc;
-  double t = -1.0;
-  if (fabs(c3) <= 1e-12) {
-    // quadratic c2 t^2 + c1 t + c0 (or linear)
-    if (fabs(c2) <= 1e-12) {
-      if (c1 < 0.0) t = (double)(-(float)c0 / (float)c1);
-    } else {
-      const double disc = c1 * c1 - 4.0 * c2 * c0;
-      if (disc >= 0.0) {
-        const float qf = -0.5f * ((float)c1 + copysignf(sqrtf((float)disc), (float)c1));
-        const float ra = qf / (float)c2, rb = (float)c0 / qf;
-        const float lo = fminf(ra, rb), hi = fmaxf(ra, rb);
-        // c2 < 0: + between the roots, so + -> - at the larger root;
-        // c2 > 0: + outside them, so + -> - at the smaller root
-        t = (double)((c2 < 0.0) ? hi : lo);
-        if (!(t > 0.0)) t = -1.0;
-      }
-    }
-  } else {
-    const double r3 = recip_refined(c3);
-    const double B = c2 * r3, C = c1 * r3, D = c0 * r3;
-    const double B3 = B * (1.0 / 3.0);
-    const double p = fma(-B, B3, C);
-    const double q = fma((2.0 / 27.0) * B * B, B, fma(-B3, C, D));
-    const double disc = fma(0.25 * q, q, (1.0 / 27.0) * p * p * p);
-    const float pf = (float)p, qf = (float)q, B3f = (float)B3;
-    if (disc > 0.0) {
-      if (c3 < 0.0) {
-        const float u = -copysignf(cbrtf(0.5f * fabsf(qf) + sqrtf((float)disc)), qf);
-        t = (double)((u != 0.0f ? u - pf / (3.0f * u) : 0.0f) - B3f);
-      }
-    } else if (p < 0.0) {
-      // roots m cos(phi - 2 pi k / 3) - B/3: k = 0 largest, k = 1 middle, k = 2 smallest
-      const float m = 2.0f * sqrtf(-pf * (1.0f / 3.0f));
-      const float arg = fminf(1.0f, fmaxf(-1.0f, 3.0f * qf / (pf * m)));
-      const float phi = acosf(arg) * (1.0f / 3.0f);
-      const float two_pi_3 = 2.09439510239319549f;
-      if (c3 < 0.0) {
-        // (the hardware cosine is accurate enough for a start the polish refines)
-        const float r1 = m * __cosf(phi - 2.0f * two_pi_3) - B3f;
-        t = (double)(r1 > 0.0f ? r1 : m * __cosf(phi) - B3f);
-      } else {
-        t = (double)(m * __cosf(phi - two_pi_3) - B3f);   // k = 1: middle root
-      }
-    } else {
-      t = -1.0;   // triple root: G'' vanishes there, so it is not a strict maximum
-    }
-  }
-  if (t > 0.0) {  // two Newton polishes on the cubic, slope inverted in FP32
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const double f = fma(fma(fma(c3, t, c2), t, c1), t, c0);
-      const double fp = fma(fma(3.0 * c3, t, 2.0 * c2), t, c1);
-      const float fpf = (float)fp;
-      if (fpf != 0.0f && isfinite(fpf)) {
-        const double tn = fma(-f, (double)(1.0f / fpf), t);
-        if (tn > 0.0 && isfinite(tn)) t = tn;
-      }
-    }
-  }
-  if (t > 0.0 && isfinite(t)) {
-    *t_out = t;
-    return true;
-  }
-  return false;
-}
-
-// exp of the twist tw = t (omega, v) in SE(3), Eq. step. The coefficients
-// sin(th)/th, (1 - cos th)/th^2 and (th - sin th)/th^3 are even functions of
-// th; below th = 0.5 they are summed as Taylor series in th^2 (truncation
-// error < 1e-16), above it from sin and cos.
-__device__ void exp_se3(const double tw[6], double dR[9], double dT[3]) {
-  const double* phi = tw;
-  const double* rho = tw + 3;
-  const double x = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
-  double A, B, C;
-  if (x < 0.25) {
-    A = 1.0 + x * (-1.0 / 6 + x * (1.0 / 120 + x * (-1.0 / 5040 + x * (1.0 / 362880 +
-        x * (-1.0 / 39916800 + x * (1.0 / 6227020800.0))))));
-    B = 0.5 + x * (-1.0 / 24 + x * (1.0 / 720 + x * (-1.0 / 40320 + x * (1.0 / 3628800 +
-        x * (-1.0 / 479001600 + x * (1.0 / 87178291200.0))))));
-    C = 1.0 / 6 + x * (-1.0 / 120 + x * (1.0 / 5040 + x * (-1.0 / 362880 + x * (1.0 / 39916800 +
-        x * (-1.0 / 6227020800.0 + x * (1.0 / 1307674368000.0))))));
-  } else {
-    const double th = sqrt(x);
-    const double s = sin(th), hs = sin(0.5 * th);
-    A = s / th;
-    B = 2.0 * hs * hs / x;
-    C = (th - s) / (x * th);
-  }
-  const double W[9] = {0.0, -phi[2], phi[1], phi[2], 0.0, -phi[0], -phi[1], phi[0], 0.0};
-  double W2[9];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
-  double V[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const double I = (i % 4 == 0) ? 1.0 : 0.0;
-    dR[i] = I + A * W[i] + B * W2[i];
-    V[i] = I + B * W[i] + C * W2[i];
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    dT[i] = V[3 * i] * rho[0] + V[3 * i + 1] * rho[1] + V[3 * i + 2] * rho[2];
-}
-
-// Gradient tail: sums (F, omega', v, pairs, candidates) -> F, metric
-// gradient, unit step direction in the centred frame.
-__device__ void finish_gradient(BlockCtx& b, const double sums[9]) {
-  const double s2 = b.tc.sigma2;
-  const double v[3] = {sums[4], sums[5], sums[6]};
-  double cxv[3];
-  cross3d(b.tc.cX, v, cxv);
-  const double ka = s2 * b.inv_l2 * b.tc.inv_a2, kb = s2 * b.inv_l2 * b.tc.inv_b2;
-  double nrm2 = 0.0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    b.xi[a] = (sums[1 + a] + cxv[a]) * ka;
-    b.xi[3 + a] = v[a] * kb;
-  }
-#pragma unroll
-  for (int a = 0; a < 6; ++a) nrm2 += b.xi[a] * b.xi[a];
-  // |xi| and 1/|xi|: FP32 rsqrt refined by two FP64 Newton steps
-  // y <- y (1.5 - 0.5 x y^2) (relative error 1e-7 -> 1e-14 -> 1e-28)
-  double inv = 0.0, nrm = 0.0;
-  if (nrm2 > 0.0 && nrm2 < 1e300) {
-    inv = (double)rsqrtf((float)nrm2);
-    if (inv > 0.0 && isfinite(inv)) {
-      inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
-      inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
-      nrm = nrm2 * inv;
-    } else {
-      nrm = sqrt(nrm2);
-      inv = 1.0 / nrm;
-    }
-  } else if (nrm2 > 0.0) {
-    nrm = sqrt(nrm2);
-    inv = 1.0 / nrm;
-  }
-  b.xi_norm = nrm;
-  b.F = s2 * sums[0];
-  b.nnz_grad = (unsigned long long)sums[7];
-  b.cand_grad = (unsigned long long)sums[8];
-  double wxc[3];
-  cross3d(b.xi, b.tc.cX, wxc);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    b.om[a] = (float)(b.xi[a] * inv);
-    b.vc[a] = (float)((b.xi[3 + a] + wxc[a]) * inv);
-  }
-}
-
-// Step tail: S0..S4, step length, pose update, stop test.
-__device__ void finish_step(BlockCtx& b, const double sums[7]) {
-  const TailConst& tc = b.tc;
-  const double nxi = b.xi_norm;
-  double pw = tc.sigma2;
-#pragma unroll
-  for (int m = 0; m < 5; ++m) {  // the sums were taken along xi / |xi|
-    b.S[m] = sums[m] * pw;
-    pw *= nxi;
-  }
-  b.nnz_total += b.nnz_grad + (unsigned long long)sums[5];
-  b.cand_total += b.cand_grad + (unsigned long long)sums[6];
-  if (tc.mode == kModeEval) {
-    b.done = 1;
-    return;
-  }
-  double t;
-  if (!(nxi > 0.0) || !(b.S[1] > 0.0)) {
-    t = 0.0;
-    b.no_ascent += 1;
-  } else {
-    bool ok;
-    if (tc.step_order == 2) {
-      ok = b.S[2] < 0.0;
-      t = ok ? -b.S[1] / (2.0 * b.S[2]) : 0.0;
-    } else {
-      ok = first_maximiser(b.S[1], 2.0 * b.S[2], 3.0 * b.S[3], 4.0 * b.S[4], &t);
-    }
-    if (!ok) {
-      b.fallback += 1;
-      t = b.have_t_prev ? 0.5 * b.t_prev : 1e-3 / nxi;
-    }
-  }
-  // P <- exp(t xi) P
-  double tw[6], dR[9], dT[3];
-#pragma unroll
-  for (int a = 0; a < 6; ++a) tw[a] = t * b.xi[a];
-  exp_se3(tw, dR, dT);
-  double Pn[12];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-      Pn[4 * r + c] = dR[3 * r] * b.P[c] + dR[3 * r + 1] * b.P[4 + c] + dR[3 * r + 2] * b.P[8 + c];
-    Pn[4 * r + 3] += dT[r];
-  }
-#pragma unroll
-  for (int i = 0; i < 12; ++i) b.P[i] = Pn[i];
-  b.t = t;
-  b.t_prev = t;
-  b.have_t_prev = 1;
-  const bool conv = (b.ell == tc.ell_floor) &&
-                    (fabs(t) * nxi < tc.eps_pose || nxi < tc.eps_grad);
-  b.k += 1;
-  if (conv || b.k >= tc.max_iters) {
-    b.done = 1;
-    b.converged = conv ? 1 : 0;
-  }
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Release the barrier of generation g (thread 0 of the last block to arrive).
-__device__ __forceinline__ void barrier_release(SolveState* st, unsigned g) {
-  atomicExch(&st->bar_count, 0u);
-  __threadfence();
-  st_release_u32(&st->bar_gen, g + 1);
-}
-
-// Wait for generation g to be released (thread 0). A block that polls
-// kSpinLimit times raises kStatusTimeout and returns false; its team then
-// leaves the solve loop when the other blocks' own waits run out at the next
-// barrier, which the timed-out block never reaches (an error path, bounded).
-__device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned g) {
-  unsigned spins = 0;
-  while (ld_acquire(&st->bar_gen) == g) {
-    if (++spins > kSpinLimit) {
-      atomicOr(&st->status, (int)kStatusTimeout);
-      return false;
-    }
-    __nanosleep(32);
-  }
-  return true;
-}
-
-// Bounded barrier of the team's nblk blocks. Every block calls it the same
-// number of times; all blocks are resident (cooperative launch).
-__device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned g = gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-    int ok = 1;
-    if (arrived == (unsigned)nblk - 1) {
-      barrier_release(st, g);
-    } else {
-      ok = barrier_wait(st, g) ? 1 : 0;
-    }
-    __threadfence();
-    gen = g + 1;
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
-
-// Fixed-order FP64 sum of the nblk (<= 2 * kThreads) block partials: thread t
-// loads blocks t and t + kThreads of every value at once (one L2 round trip),
-// then a shuffle tree per warp and the warps in order. Results land in out[]
-// (shared). Must be called by every thread of the block.
-template <class Smem>
-__device__ void reduce_partials(const double* partials, int nvals, double* out, int nblk,
-                                Smem& sm) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  double v[kPartialStride];
-#pragma unroll
-  for (int i = 0; i < kPartialStride; ++i) {
-    double a = 0.0, c = 0.0;
-    if (i < nvals) {
-      if (t < nblk) a = __ldcg(&partials[(size_t)t * kPartialStride + i]);
-      if (t + kThreads < nblk) c = __ldcg(&partials[(size_t)(t + kThreads) * kPartialStride + i]);
-    }
-    v[i] = a + c;
-  }
-#pragma unroll
-  for (int i = 0; i < kPartialStride; ++i) {
-    if (i < nvals) {
-      const double w = warp_sum_d(v[i]);
-      if (lane == 0) sm.red_d[warp][i] = w;
-    }
-  }
-  __syncthreads();
-  if (t < nvals) {
-    double r = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) r += sm.red_d[w][t];
-    out[t] = r;
-  }
-  __syncthreads();
-}
-
-// Barrier that also reduces the pass: the last block to arrive sums all block
-// partials in FP64 (fixed order, all its threads), publishes the totals and
-// then releases the others, which read the totals. Every thread of every block
-// gets the totals in sums[]. Bounded like grid_sync.
-template <class Smem>
-__device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const double* partials,
-                                 int nvals, int nblk) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-    sm.last = (arrived == (unsigned)nblk - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  const unsigned g = gen;
-  if (sm.last) {
-    reduce_partials(partials, nvals, sm.sums, nblk, sm);
-    if (threadIdx.x < (unsigned)nvals) st->red_sums[threadIdx.x] = sm.sums[threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      barrier_release(st, g);
-      sm.flag = 1;
-    }
-  } else {
-    if (threadIdx.x == 0) {
-      sm.flag = barrier_wait(st, g) ? 1 : 0;
-      __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x < (unsigned)nvals) sm.sums[threadIdx.x] = __ldcg(&st->red_sums[threadIdx.x]);
-  }
-  gen = g + 1;
-  __syncthreads();
-  return sm.flag != 0;
-}
-
-// Start of a queued solve: wait until every block of the team has claimed its
-// slot. Blocks of a team come free at different times (each finishes the pair
-// it held), so this wait can last as long as one pair's solve; it is bounded
-// by kJoinLimitNs of the global timer, after which the pair fails with
-// kStatusTimeout.
-template <class Smem>
-__device__ bool team_join(SolveState* st, int team_size, Smem& sm) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    atomicAdd(&st->join_count, 1u);
-    const unsigned long long t_start = globaltimer();
-    unsigned polls = 0;
-    while (ld_acquire(&st->join_count) < (unsigned)team_size) {
-      if ((++polls & 255u) == 0 && globaltimer() - t_start > kJoinLimitNs) {
-        ok = 0;
-        atomicOr(&st->status, (int)kStatusTimeout);
-        break;
-      }
-      __nanosleep(256);
-    }
-    __threadfence();
-    if (ld_acquire((const unsigned*)&st->status) & kStatusTimeout) ok = 0;
-    sm.flag = ok;
-  }
-  __syncthreads();
-  return sm.flag != 0;
-}
-
-// Plan of one cluster (one warp): transform its points, bounding box, cell
-// rows within the plan radius -> segments, candidate count.
-__device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState* st, int c,
-                             int lane) {
-  const GridView& g = cfg->grids[b.level];
-  const ClusterView& cv = cfg->clusters[b.level];
-  const int p0 = cv.cstart[c];
-  const int cs = cv.cstart[c + 1] - p0;
-  const bool zv = lane < cs;
-  float zx = 0.f, zy = 0.f, zz = 0.f;
-  if (zv) {
-    const float4 p = cfg->src.xyz[p0 + lane];
-    zx = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
-    zy = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
-    zz = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
-  }
-  float blo[3] = {zv ? zx : INFINITY, zv ? zy : INFINITY, zv ? zz : INFINITY};
-  float bhi[3] = {zv ? zx : -INFINITY, zv ? zy : -INFINITY, zv ? zz : -INFINITY};
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      blo[a] = fminf(blo[a], __shfl_xor_sync(kFull, blo[a], off));
-      bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(kFull, bhi[a], off));
-    }
-  }
-  const float rp = b.rplan_f;
-  const float rp2 = rp * rp;
-  const int cx0 = max(0, cell_floor(blo[0] - rp, g.ox, g.inv_h, g.nx));
-  const int cx1 = min(g.nx - 1, cell_floor(bhi[0] + rp, g.ox, g.inv_h, g.nx));
-  const int cy0 = max(0, cell_floor(blo[1] - rp, g.oy, g.inv_h, g.ny));
-  const int cy1 = min(g.ny - 1, cell_floor(bhi[1] + rp, g.oy, g.inv_h, g.ny));
-  const int cz0 = max(0, cell_floor(blo[2] - rp, g.oz, g.inv_h, g.nz));
-  const int cz1 = min(g.nz - 1, cell_floor(bhi[2] + rp, g.oz, g.inv_h, g.nz));
-  const int nyr = cy1 - cy0 + 1, nzr = cz1 - cz0 + 1;
-  const int nrows = (cx0 <= cx1 && nyr > 0 && nzr > 0) ? nyr * nzr : 0;
-  int* sxs = cfg->seg_xs + (size_t)c * kMaxSeg;
-  int* spf = cfg->seg_pref + (size_t)c * kMaxSeg;
-  const unsigned lt = (1u << lane) - 1u;
-  int nseg = 0, total = 0;
-  bool overflow = false;
-  for (int rb = 0; rb < nrows; rb += 32) {
-    const int r = rb + lane;
-    int len = 0, xs = 0;
-    if (r < nrows) {
-      const int cy = cy0 + r % nyr, cz = cz0 + r / nyr;
-      const float ylo = g.oy + cy * g.h, yhi = ylo + g.h;
-      const float zlo = g.oz + cz * g.h, zhi = zlo + g.h;
-      const float dy = fmaxf(0.f, fmaxf(ylo - bhi[1], blo[1] - yhi));
-      const float dz = fmaxf(0.f, fmaxf(zlo - bhi[2], blo[2] - zhi));
-      const float rem = rp2 - dy * dy - dz * dz;
-      if (rem >= 0.f) {
-        const float rx = sqrtf(rem);
-        const int a0 = max(cx0, cell_floor(blo[0] - rx, g.ox, g.inv_h, g.nx));
-        const int a1 = min(cx1, cell_floor(bhi[0] + rx, g.ox, g.inv_h, g.nx));
-        if (a0 <= a1) {
-          const int base = g.nx * (cy + g.ny * cz);
-          xs = g.cell_start[base + a0];
-          len = g.cell_start[base + a1 + 1] - xs;
-        }
-      }
-    }
-    const unsigned m = __ballot_sync(kFull, len > 0);
-    const int idx = nseg + __popc(m & lt);
-    const int keep = (len > 0 && idx < kMaxSeg) ? len : 0;
-    if (len > 0 && idx >= kMaxSeg) overflow = true;
-    int incl = keep;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int v = __shfl_up_sync(kFull, incl, off);
-      if (lane >= off) incl += v;
-    }
-    if (keep > 0) {
-      sxs[idx] = xs;
-      spf[idx] = total + incl - keep;
-    }
-    nseg += __popc(m);
-    total += __shfl_sync(kFull, incl, 31);
-  }
-  if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&st->status, (int)kStatusSegOverflow);
-  if (lane == 0) {
-    cfg->cl_nseg[c] = min(nseg, kMaxSeg);
-    cfg->cl_cand[c] = total;
-    cfg->cl_kept[c] = 0;
-  }
-}
-
-// Work of cluster c under the current plan, in pair-test units: staging the
-// cluster costs cost_cluster, each 32-candidate chunk its cs4 pair tests per
-// lane (cluster size padded to a multiple of 4) plus cost_chunk of per-chunk
-// overhead, plus (use_kept, once the plan's first gradient pass has counted
-// them) cost_kept per kept pair of the cluster, spread evenly over its chunks.
-// Chunk j starts at offset cost_cluster + j * k, k = the per-chunk cost.
-__device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const ClusterView& cv,
-                                                  int c, int* k_out, bool use_kept) {
-  const int tc = __ldcg(&cfg->cl_cand[c]);
-  const int cs4 = ((cv.cstart[c + 1] - cv.cstart[c]) + 3) & ~3;
-  const int nch = (tc + 31) >> 5;
-  int k = cs4 + cfg->cost_chunk;
-  if (use_kept && nch > 0)
-    k += (int)(cfg->cost_kept * (float)__ldcg(&cfg->cl_kept[c]) / (float)nch);
-  *k_out = k;
-  return nch > 0 ? (long long)cfg->cost_cluster + (long long)nch * k : 0;
-}
-
-// Shared memory of the solve kernel.
-template <int DPS, int NU>
-struct SolveSmem {
-  float4 z[kWarps][kClusterMax];
-  float zf[kWarps][DPS][kClusterMax];
-  float4 u[kWarps][NU][kClusterMax];
-  int xs[kWarps][kMaxSeg];
-  int pf[kWarps][kMaxSeg + 1];
-  float red[kWarps][10];
-  double red_d[kWarps][kPartialStride];
-  long long scan[kThreads];
-  long long bnd_base[2 * kWarps];   // work offset of the group holding each warp boundary
-  int bnd_group[2 * kWarps];
-  double sums[10];
-  int flag, last;
-  long long q_slot;                 // queue: claimed slot (-1: none left)
-  int q_entry;                      //        entry that slot belongs to
-  short cache_n[kWarps];            // slots cached per warp (-1: streamed)
-  unsigned short cache_hdr[kWarps][32];
-  int cache_cl[kWarps][32];         // cluster of each cached cluster slot
-  BlockCtx b;
-};
-
-// (cluster, chunk) of the first chunk whose work starts at or after s, for s
-// inside group `group` whose work starts at `base` (one warp). The chunk may
-// equal the cluster's chunk count, which means the next cluster's first chunk.
-__device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, long long base,
-                       long long s, int lane, int* c_out, int* j_out, bool use_kept) {
-  const int c = group * 32 + lane;
-  long long w = 0;
-  int kk = 4;
-  if (c < cv.ncl) w = cluster_work(cfg, cv, c, &kk, use_kept);
-  long long incl = w;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const long long v = __shfl_up_sync(kFull, incl, off);
-    if (lane >= off) incl += v;
-  }
-  const long long excl = base + incl - w;
-  const unsigned m = __ballot_sync(kFull, c < cv.ncl && w > 0 && s >= excl && s < excl + w);
-  if (m) {
-    const int src = __ffs(m) - 1;
-    const long long e = __shfl_sync(kFull, excl, src) + cfg->cost_cluster;
-    const int k4 = __shfl_sync(kFull, kk, src);
-    *c_out = group * 32 + src;
-    *j_out = s <= e ? 0 : (int)((s - e + k4 - 1) / k4);
-  } else {
-    *c_out = min(group * 32 + 32, cv.ncl);
-    *j_out = 0;
-  }
-}
-
-// Place the block's warps on an even split of the plan's work: warp w owns the
-// chunks whose work starts in [floor(w TW/NW), floor((w+1) TW/NW)).
-template <int DPS, int NU>
-__device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid, Team team) {
-  const ClusterView& cv = cfg->clusters[sm.b.level];
-  const int ng = (cv.ncl + 31) / 32;
-  const int per = (ng + kThreads - 1) / kThreads;
-  const int g0 = min(ng, tid * per), g1 = min(ng, g0 + per);
-  long long local = 0;
-  for (int gi = g0; gi < g1; ++gi) local += __ldcg(&cfg->group_agg[gi]);
-  sm.scan[tid] = local;
-  if (tid < 2 * kWarps) sm.bnd_group[tid] = -1;
-  __syncthreads();
-  for (int off = 1; off < kThreads; off <<= 1) {
-    const long long v = tid >= off ? sm.scan[tid - off] : 0;
-    __syncthreads();
-    sm.scan[tid] += v;
-    __syncthreads();
-  }
-  const long long TW = sm.scan[kThreads - 1];
-  const long long NW = (long long)team.size * kWarps;
-  long long run = sm.scan[tid] - local;
-  for (int gi = g0; gi < g1; ++gi) {
-    const long long gtests = __ldcg(&cfg->group_agg[gi]);
-#pragma unroll
-    for (int q = 0; q < 2 * kWarps; ++q) {
-      const long long w = (long long)team.rank * kWarps + (q >> 1) + (q & 1);
-      const long long s = TW > 0 ? (w * TW) / NW : 0;
-      if (gtests > 0 && s >= run && s < run + gtests) {
-        sm.bnd_group[q] = gi;
-        sm.bnd_base[q] = run;
-      }
-    }
-    run += gtests;
-  }
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int q = 2 * warp + h;
-    const long long w = (long long)team.rank * kWarps + warp + h;
-    const long long s = TW > 0 ? (w * TW) / NW : 0;
-    int c, jj;
-    if (TW == 0 || s >= TW || sm.bnd_group[q] < 0) {
-      c = cv.ncl;   // past the end: no chunk
-      jj = 0;
-    } else {
-      locate(cfg, cv, sm.bnd_group[q], sm.bnd_base[q], s, lane, &c, &jj, sm.b.use_kept != 0);
-    }
-    if (lane == 0) {
-      if (h == 0) {
-        sm.b.w_c0[warp] = c;
-        sm.b.w_j0[warp] = jj;
-      } else {
-        sm.b.w_c1[warp] = c;
-        sm.b.w_j1[warp] = jj;
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// Stage one cluster for a warp: lane j < cs holds the cluster's centred
-// source point p and its features; the transformed point z~' = R p + T (and,
-// for the step pass, the Taylor coefficient vectors of Eq. fourth) go to the
-// warp's shared-memory slots, read by every lane of the pair loop.
-template <bool STEP, int DP, int DPS, int NU>
-__device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, int lane, bool zv,
-                                              float4 p, const float pf[DPS]) {
-  const BlockCtx& b = sm.b;
-  float4 z = make_float4(kFar, kFar, kFar, 0.f);
-  if (zv) {
-    z.x = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
-    z.y = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
-    z.z = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
-  }
-  sm.z[warp][lane] = z;
-#pragma unroll
-  for (int d = 0; d < DP; ++d) sm.zf[warp][d][lane] = zv ? pf[d] : 0.f;
-  if (STEP) {
-    const float* om = b.om;
-    const float* vc = b.vc;
-    const float inv_l2 = b.inv_l2f;
-    const float zt[3] = {zv ? z.x : 0.f, zv ? z.y : 0.f, zv ? z.z : 0.f};
-    float u1[3], u2[3], u3[3], u4[3];
-    u1[0] = om[1] * zt[2] - om[2] * zt[1] + vc[0];
-    u1[1] = om[2] * zt[0] - om[0] * zt[2] + vc[1];
-    u1[2] = om[0] * zt[1] - om[1] * zt[0] + vc[2];
-    u2[0] = om[1] * u1[2] - om[2] * u1[1];
-    u2[1] = om[2] * u1[0] - om[0] * u1[2];
-    u2[2] = om[0] * u1[1] - om[1] * u1[0];
-    u3[0] = om[1] * u2[2] - om[2] * u2[1];
-    u3[1] = om[2] * u2[0] - om[0] * u2[2];
-    u3[2] = om[0] * u2[1] - om[1] * u2[0];
-    u4[0] = om[1] * u3[2] - om[2] * u3[1];
-    u4[1] = om[2] * u3[0] - om[0] * u3[2];
-    u4[2] = om[0] * u3[1] - om[1] * u3[0];
-    const float u11 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
-    const float u12 = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
-    const float u13 = u1[0] * u3[0] + u1[1] * u3[1] + u1[2] * u3[2];
-    const float u22 = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
-    // beta = e.U1; gamma = e.U2 - k2; delta = e.U3 - k3; eps = e.U4 - k4
-    const float c1 = inv_l2, c2 = 0.5f * inv_l2, c3 = inv_l2 * (1.0f / 6.0f),
-                c4 = inv_l2 * (1.0f / 24.0f);
-    sm.u[warp][0][lane] = make_float4(u1[0] * c1, u1[1] * c1, u1[2] * c1, 0.5f * u11 * inv_l2);
-    sm.u[warp][1 % NU][lane] = make_float4(u2[0] * c2, u2[1] * c2, u2[2] * c2, 0.5f * u12 * inv_l2);
-    sm.u[warp][2 % NU][lane] = make_float4(u3[0] * c3, u3[1] * c3, u3[2] * c3,
-                                           (u13 * (1.0f / 6.0f) + u22 * 0.125f) * inv_l2);
-    sm.u[warp][3 % NU][lane] = make_float4(u4[0] * c4, u4[1] * c4, u4[2] * c4, 0.f);
-  }
-}
-
-// One 32-candidate chunk against the staged cluster: lane = candidate x'
-// (xp, features xf; padding points lie beyond every cutoff), inner loop over
-// the cluster's cs4 points (cluster size rounded up to 4; padding slots lie
-// beyond the cutoff too). FP32 pair arithmetic, one ex2.approx per pair.
-// Points are taken four at a time: the four distance tests first, then, if
-// any lane of the warp keeps any of the four pairs (one vote, so the branch
-// is uniform), the four pair bodies without branches, a rejected pair
-// contributing exactly nothing (its weight is selected to zero and its step
-// terms are not added). The four bodies are independent, so their latencies
-// overlap.
-template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ __forceinline__ void chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, float4 xp,
-                                            const float xf[DPS], int cs4, float rc2, float A,
-                                            float acc[7], unsigned& nnz) {
-  float W = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
-  for (int j0 = 0; j0 < cs4; j0 += 4) {
-    float ex[4], ey[4], ez[4], d2[4];
-    bool keep[4];
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const float4 z = sm.z[warp][j0 + jj];
-      ex[jj] = xp.x - z.x;
-      ey[jj] = xp.y - z.y;
-      ez[jj] = xp.z - z.z;
-      d2[jj] = fmaf(ex[jj], ex[jj], fmaf(ey[jj], ey[jj], ez[jj] * ez[jj]));
-      keep[jj] = d2[jj] <= rc2;
-    }
-    if (!__any_sync(kFull, keep[0] | keep[1] | keep[2] | keep[3])) continue;
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int j = j0 + jj;
-      float w;
-      if (MODE == kColorKernel) {
-        float qf = 0.f;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) {
-          const float df = xf[d] - sm.zf[warp][d][j];
-          qf = fmaf(df, df, qf);
-        }
-        w = ex2_approx(-fmaf(A, d2[jj], qf));
-      } else if (MODE == kColorDot) {
-        float cdot = 0.f;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) cdot = fmaf(xf[d], sm.zf[warp][d][j], cdot);
-        w = ex2_approx(-A * d2[jj]) * cdot;
-      } else {
-        w = ex2_approx(-A * d2[jj]);
-      }
-      w = keep[jj] ? w : 0.f;
-      nnz += keep[jj] ? 1u : 0u;
-      if (!STEP) {
-        // |e| <= 2 kFar is finite, so a zero weight adds exactly zero
-        W += w;
-        Ex = fmaf(w, ex[jj], Ex);
-        Ey = fmaf(w, ey[jj], Ey);
-        Ez = fmaf(w, ez[jj], Ez);
-      } else {
-        const float4 U1 = sm.u[warp][0][j], U2 = sm.u[warp][1 % NU][j];
-        const float4 U3 = sm.u[warp][2 % NU][j], U4 = sm.u[warp][3 % NU][j];
-        const float beta = fmaf(ex[jj], U1.x, fmaf(ey[jj], U1.y, ez[jj] * U1.z));
-        const float gam = fmaf(ex[jj], U2.x, fmaf(ey[jj], U2.y, fmaf(ez[jj], U2.z, -U1.w)));
-        const float del = fmaf(ex[jj], U3.x, fmaf(ey[jj], U3.y, fmaf(ez[jj], U3.z, -U2.w)));
-        const float eps = fmaf(ex[jj], U4.x, fmaf(ey[jj], U4.y, fmaf(ez[jj], U4.z, -U3.w)));
-        const float b2 = beta * beta;
-        const float g2 = fmaf(0.5f, b2, gam);
-        const float g3 = fmaf(beta, fmaf(b2, 1.0f / 6.0f, gam), del);
-        const float g4 = fmaf(b2 * b2, 1.0f / 24.0f,
-                              fmaf(0.5f * gam, b2 + gam, fmaf(beta, del, eps)));
-        // the polynomial of a far padding pair may overflow: select, not scale
-        acc[0] += w;
-        acc[1] = keep[jj] ? fmaf(w, beta, acc[1]) : acc[1];
-        acc[2] = keep[jj] ? fmaf(w, g2, acc[2]) : acc[2];
-        acc[3] = keep[jj] ? fmaf(w, g3, acc[3]) : acc[3];
-        acc[4] = keep[jj] ? fmaf(w, g4, acc[4]) : acc[4];
-      }
-    }
-  }
-  if (!STEP) {
-    // x' fixed per lane: sum_j w (z~'_j x e_ij) = x' x E_i
-    acc[0] += W;
-    acc[1] += xp.y * Ez - xp.z * Ey;
-    acc[2] += xp.z * Ex - xp.x * Ez;
-    acc[3] += xp.x * Ey - xp.y * Ex;
-    acc[4] += Ex;
-    acc[5] += Ey;
-    acc[6] += Ez;
-  }
-}
-
-// Segments of cluster c into the warp's shared arrays, and the segment that
-// holds candidate q0 (binary search over the candidate offsets).
-template <int DPS, int NU>
-__device__ __forceinline__ int load_segments(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
-                                             int lane, int c, int tc, int q0) {
-  const int nseg = __ldcg(&cfg->cl_nseg[c]);
-  for (int i = lane; i < nseg; i += 32) {
-    sm.xs[warp][i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
-    sm.pf[warp][i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
-  }
-  if (lane == 0) sm.pf[warp][nseg] = tc;
-  __syncwarp();
-  int lo = 0, hi = nseg;
-  if (q0 < tc) {
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (sm.pf[warp][mid] <= q0) lo = mid;
-      else hi = mid;
-    }
-  }
-  return lo;
-}
-
-// Candidate q of the staged cluster (padding beyond tc), advancing seg.
-template <int DP, int DPS, int NU>
-__device__ __forceinline__ float4 load_candidate(const GridView& g, SolveSmem<DPS, NU>& sm, int warp,
-                                                 int q, int tc, int& seg, float xf[DPS]) {
-  float4 xp = make_float4(-kFar, -kFar, -kFar, 0.f);
-#pragma unroll
-  for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
-  if (q < tc) {
-    while (sm.pf[warp][seg + 1] <= q) ++seg;
-    const int xi = sm.xs[warp][seg] + (q - sm.pf[warp][seg]);
-    xp = g.xyz[xi];
-#pragma unroll
-    for (int d = 0; d < DP; ++d) xf[d] = g.feat[d * g.n_pad + xi];
-  }
-  return xp;
-}
-
-// Kept pairs of cluster c counted by this warp, added to the plan's
-// per-cluster totals (one atomic per warp and cluster).
-__device__ __forceinline__ void add_kept(const SolveCfg* cfg, int c, unsigned kept, int lane) {
-  unsigned k = kept;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) k += __shfl_down_sync(kFull, k, off);
-  if (lane == 0 && c >= 0 && k) atomicAdd(&cfg->cl_kept[c], (int)k);
-}
-
-// One warp's share of a pair pass, streamed from global memory (L2): lane
-// sums in acc, counts in nnz / cand.
-template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ void pass_stream(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
-                            float acc[7], unsigned& nnz, unsigned& cand) {
-  const BlockCtx& b = sm.b;
-  const GridView& g = cfg->grids[b.level];
-  const ClusterView& cv = cfg->clusters[b.level];
-  const float rc2 = b.rc2, A = b.A;
-  int c = b.w_c0[warp], jc = b.w_j0[warp];
-  const int c_end = b.w_c1[warp], j_end = b.w_j1[warp];
-  int loaded = -1, cs = 0, cs4 = 0, tc = 0, nch_c = 0, seg = 0;
-  float4 xp_next = make_float4(-kFar, -kFar, -kFar, 0.f);
-  float xf_next[DPS];
-#pragma unroll
-  for (int d = 0; d < DPS; ++d) xf_next[d] = 0.f;
-  bool have_next = false;
-  const bool collect = !STEP && b.collect_kept;
-  unsigned nnz0 = nnz;
-  for (;;) {
-    if (c != loaded) {
-      if (collect) {
-        add_kept(cfg, loaded, nnz - nnz0, lane);
-        nnz0 = nnz;
-      }
-      for (;;) {  // the next cluster that still has a chunk in this warp's range
-        if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) return;
-        tc = __ldcg(&cfg->cl_cand[c]);
-        nch_c = (tc + 31) >> 5;
-        if (jc < nch_c) break;
-        ++c;
-        jc = 0;
-      }
-      __syncwarp();   // every lane is done with the previous cluster's staging
-      const int p0 = cv.cstart[c];
-      cs = cv.cstart[c + 1] - p0;
-      const bool zv = lane < cs;
-      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      float pf[DPS];
-#pragma unroll
-      for (int d = 0; d < DPS; ++d) pf[d] = 0.f;
-      if (zv) {
-        p = cfg->src.xyz[p0 + lane];
-#pragma unroll
-        for (int d = 0; d < DP; ++d) pf[d] = cfg->src.feat[d * cfg->src.m_pad + p0 + lane];
-      }
-      stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, zv, p, pf);
-      cs4 = (cs + 3) & ~3;
-      loaded = c;
-      have_next = false;
-      seg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, jc * 32 + lane);
-    }
-    // candidate of chunk jc (prefetched during the previous chunk of the same
-    // cluster) and the prefetch of chunk jc + 1
-    float4 xp;
-    float xf[DPS];
-    if (have_next) {
-      xp = xp_next;
-#pragma unroll
-      for (int d = 0; d < DPS; ++d) xf[d] = xf_next[d];
-    } else {
-      xp = load_candidate<DP, DPS, NU>(g, sm, warp, jc * 32 + lane, tc, seg, xf);
-    }
-    if (jc * 32 + lane < tc) cand += (unsigned)cs;
-    const bool last_of_range = (c == c_end && jc + 1 >= j_end);
-    have_next = (jc + 1 < nch_c) && !last_of_range;
-    if (have_next) xp_next = load_candidate<DP, DPS, NU>(g, sm, warp, (jc + 1) * 32 + lane, tc, seg,
-                                                         xf_next);
-    chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, cs4, rc2, A, acc, nnz);
-    if (last_of_range) {
-      if (collect) add_kept(cfg, loaded, nnz - nnz0, lane);
-      return;
-    }
-    if (++jc >= nch_c) {
-      ++c;
-      jc = 0;
-    }
-  }
-}
-
-// Shared-memory cache of a warp's share of the plan. A slot holds 32 points
-// (float4 xyz, then DP feature planes of 32 floats): either the raw centred
-// source points of a cluster (header kSlotCluster | cluster size) or the 32
-// candidates of a chunk (header = number of valid candidates; the rest are
-// padding points beyond every cutoff). Filled once per plan when the warp's
-// whole share fits, so that the passes of every iteration that reuses the
-// plan (at the lengthscale floor, most of the solve) read no global memory.
-constexpr int kCacheSlots = 32;                 // header capacity per warp
-constexpr unsigned short kSlotCluster = 0x8000;
-
-template <int DP>
-__device__ __forceinline__ constexpr int slot_floats() {
-  return 32 * (4 + DP);
-}
-
-template <int DP, int DPS, int NU>
-__device__ void fill_cache(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
-                           float* cache, int slots) {
-  const BlockCtx& b = sm.b;
-  const GridView& g = cfg->grids[b.level];
-  const ClusterView& cv = cfg->clusters[b.level];
-  const int c0 = b.w_c0[warp], j0 = b.w_j0[warp];
-  const int c_end = b.w_c1[warp], j_end = b.w_j1[warp];
-  // count the slots the share needs
-  int need = 0;
-  {
-    int c = c0, jc = j0;
-    for (;;) {
-      if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) break;
-      const int nch = (__ldcg(&cfg->cl_cand[c]) + 31) >> 5;
-      if (jc < nch) {
-        const int jl = (c == c_end) ? min(nch, j_end) : nch;
-        need += 1 + (jl - jc);
-      }
-      ++c;
-      jc = 0;
-    }
-  }
-  if (need > min(slots, kCacheSlots)) {
-    if (lane == 0) sm.cache_n[warp] = -1;
-    __syncwarp();
-    return;
-  }
-  float* base = cache + (size_t)warp * slots * slot_floats<DP>();
-  int n = 0;
-  int c = c0, jc = j0;
-  for (;;) {
-    if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) break;
-    const int tc = __ldcg(&cfg->cl_cand[c]);
-    const int nch = (tc + 31) >> 5;
-    if (jc < nch) {
-      const int jl = (c == c_end) ? min(nch, j_end) : nch;
-      const int p0 = cv.cstart[c];
-      const int cs = cv.cstart[c + 1] - p0;
-      float* sl = base + (size_t)n * slot_floats<DP>();
-      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (lane < cs) p = cfg->src.xyz[p0 + lane];
-      reinterpret_cast<float4*>(sl)[lane] = p;
-#pragma unroll
-      for (int d = 0; d < DP; ++d)
-        sl[128 + d * 32 + lane] = lane < cs ? cfg->src.feat[d * cfg->src.m_pad + p0 + lane] : 0.f;
-      if (lane == 0) {
-        sm.cache_hdr[warp][n] = (unsigned short)(kSlotCluster | cs);
-        sm.cache_cl[warp][n] = c;
-      }
-      ++n;
-      int seg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, jc * 32 + lane);
-      for (int k = jc; k < jl; ++k) {
-        float xf[DPS];
-        const float4 xp = load_candidate<DP, DPS, NU>(g, sm, warp, k * 32 + lane, tc, seg, xf);
-        float* sk = base + (size_t)n * slot_floats<DP>();
-        reinterpret_cast<float4*>(sk)[lane] = xp;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) sk[128 + d * 32 + lane] = xf[d];
-        if (lane == 0) sm.cache_hdr[warp][n] = (unsigned short)min(32, tc - k * 32);
-        ++n;
-      }
-      __syncwarp();   // the segment arrays are reused by the next cluster
-    }
-    ++c;
-    jc = 0;
-  }
-  if (lane == 0) sm.cache_n[warp] = (short)n;
-  __syncwarp();
-}
-
-// The same share as pass_stream, from the warp's cache.
-template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
-                            const float* cache, int slots, float acc[7], unsigned& nnz,
-                            unsigned& cand) {
-  const float rc2 = sm.b.rc2, A = sm.b.A;
-  const bool collect = !STEP && sm.b.collect_kept;
-  const float* base = cache + (size_t)warp * slots * slot_floats<DP>();
-  const int n = sm.cache_n[warp];
-  int cs = 0, cs4 = 0, cur = -1;
-  unsigned nnz0 = nnz;
-  for (int s = 0; s < n; ++s) {
-    const unsigned h = sm.cache_hdr[warp][s];
-    const float* sl = base + (size_t)s * slot_floats<DP>();
-    const float4 p = reinterpret_cast<const float4*>(sl)[lane];
-    float f[DPS];
-#pragma unroll
-    for (int d = 0; d < DPS; ++d) f[d] = d < DP ? sl[128 + d * 32 + lane] : 0.f;
-    if (h & kSlotCluster) {
-      if (collect) {
-        add_kept(cfg, cur, nnz - nnz0, lane);
-        cur = sm.cache_cl[warp][s];
-        nnz0 = nnz;
-      }
-      __syncwarp();   // every lane is done with the previous cluster
-      cs = (int)(h & 0xff);
-      stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, lane < cs, p, f);
-      cs4 = (cs + 3) & ~3;
-      __syncwarp();
-    } else {
-      if (lane < (int)h) cand += (unsigned)cs;
-      chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, p, f, cs4, rc2, A, acc, nnz);
-    }
-  }
-  if (collect) add_kept(cfg, cur, nnz - nnz0, lane);
-}
-
-template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ __forceinline__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
-                                          int lane, const float* cache, int slots, float acc[7],
-                                          unsigned& nnz, unsigned& cand) {
-  if (sm.cache_n[warp] >= 0)
-    pass_cached<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots, acc, nnz, cand);
-  else
-    pass_stream<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, acc, nnz, cand);
-}
-
-// One pass over the block's warps, then the block partial (fixed order).
-template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials, int rank,
-                         const float* cache, int slots) {
-  constexpr int NACC = STEP ? 5 : 7;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float acc[7];
-#pragma unroll
-  for (int i = 0; i < 7; ++i) acc[i] = 0.f;
-  unsigned nnz = 0, cand = 0;
-  pass_warp<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots, acc, nnz, cand);
-  __syncwarp();
-#pragma unroll
-  for (int i = 0; i < NACC; ++i) {
-    const float v = warp_sum_f(acc[i]);
-    if (lane == 0) sm.red[warp][i] = v;
-  }
-  unsigned wn = nnz, wc = cand;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    wn += __shfl_down_sync(kFull, wn, off);
-    wc += __shfl_down_sync(kFull, wc, off);
-  }
-  if (lane == 0) {
-    sm.red[warp][NACC] = __uint_as_float(wn);
-    sm.red[warp][NACC + 1] = __uint_as_float(wc);
-  }
-  __syncthreads();
-  if (warp == 0 && lane < NACC + 2) {
-    double s = 0.0;
-    if (lane < NACC) {
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += (double)sm.red[w][lane];
-    } else {
-      unsigned long long n = 0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) n += __float_as_uint(sm.red[w][lane]);
-      s = (double)n;
-    }
-    partials[(size_t)rank * kPartialStride + lane] = s;
-  }
-}
-
-__device__ void publish(SolveState* st, const BlockCtx& b) {
-  for (int i = 0; i < 16; ++i) st->P[i] = b.P[i];
-  for (int i = 0; i < 6; ++i) st->xi[i] = b.xi[i];
-  for (int i = 0; i < 5; ++i) st->S[i] = b.S[i];
-  st->xi_norm = b.xi_norm;
-  st->F = b.F;
-  st->t = b.t;
-  st->ell = b.ell;
-  st->level = b.level;
-  st->iter = b.k;
-  st->done = b.done;
-  st->converged = b.converged;
-  st->fallback_steps = b.fallback;
-  st->no_ascent_steps = b.no_ascent;
-  st->nnz_total = b.nnz_total;
-  st->cand_total = b.cand_total;
-  st->nnz_eval = b.nnz_grad;
-  st->cand_eval = b.cand_grad;
-}
-
-// The whole solve of one pair (or one evaluation) by one team of blocks.
-template <int DP, int MODE, int DPS, int NU>
-__device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
-                           double* __restrict__ partials, IterRecord* __restrict__ records,
-                           Team team, SolveSmem<DPS, NU>& sm, bool join, float* cache,
-                           int slots) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned gen = 0;
-  double* part_g = partials;
-  double* part_s = partials + (size_t)team.size * kPartialStride;
-  const long long NW = (long long)team.size * kWarps;
-  const long long gw = (long long)team.rank * kWarps + warp;
-
-  if (tid == 0) {
-    BlockCtx& b = sm.b;
-    TailConst& tc = b.tc;
-    for (int a = 0; a < 3; ++a) {
-      tc.cX[a] = cfg->cX[a];
-      tc.cZ[a] = cfg->cZ[a];
-    }
-    tc.sigma2 = cfg->sigma2;
-    tc.inv_a2 = 1.0 / cfg->a2;
-    tc.inv_b2 = 1.0 / cfg->b2;
-    tc.ell_floor = cfg->ell_floor;
-    tc.eps_pose = cfg->eps_pose;
-    tc.eps_grad = cfg->eps_grad;
-    tc.src_radius = cfg->src_radius;
-    tc.mode = cfg->mode;
-    tc.step_order = cfg->step_order;
-    tc.max_iters = cfg->max_iters;
-    for (int i = 0; i < 16; ++i) b.P[i] = st->P0[i];
-    b.k = 0;
-    b.level = 0;
-    b.plan_level = -1;
-    b.need_plan = 1;
-    b.done = cfg->max_iters <= 0 ? 1 : 0;
-    b.converged = b.fallback = b.no_ascent = b.have_t_prev = 0;
-    b.use_kept = b.collect_kept = b.rebalance = 0;
-    b.t = b.t_prev = 0.0;
-    b.nnz_total = b.cand_total = b.nnz_grad = b.cand_grad = 0;
-    b.F = b.xi_norm = 0.0;
-    for (int i = 0; i < 6; ++i) b.xi[i] = 0.0;
-    for (int i = 0; i < 5; ++i) b.S[i] = 0.0;
-    b.r_plan = 0.0;
-    b.plan_ell = 0.0;
-    if (!b.done) begin_iteration(cfg->iters[0], b);
-  }
-  __syncthreads();
-  if (join && !team_join(st, team.size, sm)) {
-    if (tid == 0) sm.b.done = 1;   // a team that never assembled runs no iteration
-    __syncthreads();
-  }
-  if (team.rank == 0 && tid == 0) st->t_begin_ns = globaltimer();
-
-  while (!sm.b.done) {
-    unsigned long long t0 = 0, t1 = 0, t2 = 0, tg1 = 0, tg2 = 0, ts1 = 0, ts2 = 0;
-    const bool stamp = records != nullptr && team.rank == 0 && tid == 0;
-    if (stamp) t0 = globaltimer();
-    const int replan = sm.b.need_plan;
-    // a new plan, or the one rebalance of a plan that is being reused: its
-    // work split redone with the kept pairs its first gradient pass counted
-    const int rebalance = !replan && sm.b.rebalance;
-    if (replan || rebalance) {
-      const ClusterView& cv = cfg->clusters[sm.b.level];
-      if (replan) {
-        for (long long c = gw; c < cv.ncl; c += NW) plan_cluster(cfg, sm.b, st, (int)c, lane);
-        if (!grid_sync(st, gen, &sm.flag, team.size)) break;
-      }
-      if (tid == 0) sm.b.use_kept = rebalance;
-      __syncthreads();
-      const int ng = (cv.ncl + 31) / 32;
-      for (long long gi = gw; gi < ng; gi += NW) {
-        const int c = (int)gi * 32 + lane;
-        int kk;
-        long long w = c < cv.ncl ? cluster_work(cfg, cv, c, &kk, rebalance != 0) : 0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(kFull, w, off);
-        if (lane == 0) cfg->group_agg[gi] = w;
-      }
-      if (!grid_sync(st, gen, &sm.flag, team.size)) break;
-      split_work<DPS, NU>(cfg, sm, tid, team);
-      fill_cache<DP, DPS, NU>(cfg, sm, warp, lane, cache, slots);
-      if (tid == 0) {
-        sm.b.need_plan = 0;
-        sm.b.collect_kept = replan && cfg->cost_kept > 0.f;
-        sm.b.rebalance = sm.b.collect_kept;
-        if (rebalance) sm.b.rebalance = 0;
-      }
-      __syncthreads();
-    }
-    if (stamp) t1 = globaltimer();
-    // ---- gradient pass ----
-    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g, team.rank, cache, slots);
-    if (stamp) tg1 = globaltimer();
-    if (!grid_sync_reduce(st, gen, sm, part_g, 9, team.size)) break;
-    if (stamp) tg2 = globaltimer();
-    if (tid == 0) {
-      sm.b.collect_kept = 0;
-      finish_gradient(sm.b, sm.sums);
-    }
-    __syncthreads();
-    if (stamp) t2 = globaltimer();
-    // ---- step pass ----
-    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s, team.rank, cache, slots);
-    if (stamp) ts1 = globaltimer();
-    if (!grid_sync_reduce(st, gen, sm, part_s, 7, team.size)) break;
-    if (stamp) ts2 = globaltimer();
-    {
-      if (tid == 0) {
-        BlockCtx& b = sm.b;
-        const int k = b.k;
-        // the next iteration's constants, loaded now and used after the tail
-        const IterConst ic_next = cfg->iters[min(k + 1, b.tc.max_iters - 1)];
-        const unsigned long long pairs_before = b.nnz_total;
-        finish_step(b, sm.sums);
-        if (stamp && k < b.tc.max_iters) {
-          IterRecord& r = records[k];
-          r.ell = b.ell;
-          r.t_plan_ns = (float)(t1 - t0);
-          r.t_grad_ns = (float)(t2 - t1);
-          r.t_step_ns = (float)(globaltimer() - t2);
-          r.t_grad_pass_ns = (float)(tg1 - t1);
-          r.t_grad_sync_ns = (float)(tg2 - t1);
-          r.t_step_pass_ns = (float)(ts1 - t2);
-          r.t_step_sync_ns = (float)(ts2 - t2);
-          r.replanned = replan;
-          r.grad_pairs = (long long)b.nnz_grad;
-          r.step_pairs = (long long)(b.nnz_total - pairs_before - b.nnz_grad);
-          r.grad_candidates = (long long)b.cand_grad;
-        }
-        if (!b.done) begin_iteration(ic_next, b);
-      }
-    }
-    __syncthreads();
-  }
-  if (team.rank == 0 && tid == 0) {
-    publish(st, sm.b);
-    st->t_end_ns = globaltimer();
-  }
-  __syncthreads();
-}
-
-// The whole solve (or one evaluation) in one cooperative launch: the grid is
-// one team.
-template <int DP, int MODE>
-__global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
-solve_kernel(const SolveCfg* __restrict__ cfg, SolveState* __restrict__ st,
-             double* __restrict__ partials, IterRecord* __restrict__ records, int cache_slots) {
-  constexpr int DPS = DP > 0 ? DP : 1;
-  constexpr int NU = 4;
-  __shared__ SolveSmem<DPS, NU> sm;
-  extern __shared__ float4 dyn_smem[];
-  solve_pair<DP, MODE, DPS, NU>(cfg, st, partials, records, Team{(int)blockIdx.x, (int)gridDim.x},
-                                sm, false, reinterpret_cast<float*>(dyn_smem), cache_slots);
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed_sys_u64(const void* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_sys_s32(int* p, int v) {
-  asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Entry fields read at system scope: the entries of a served queue live in
-// host memory that the host appends to while the kernel runs.
-__device__ QueueEntry load_entry(const QueueEntry* e) {
-  static_assert(sizeof(QueueEntry) == 40, "QueueEntry layout");
-  QueueEntry r;
-  unsigned long long w[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) w[i] = ld_relaxed_sys_u64(reinterpret_cast<const unsigned long long*>(e) + i);
-  memcpy(&r, w, sizeof(r));
-  return r;
-}
-
-// Claim the next slot (thread 0): slots are handed out in order, so every
-// slot of an entry is claimed before any slot of a later one. A team whose
-// first blocks start before the rest have claimed their slots waits at its
-// first barrier; the entries ahead of it never wait on later ones, so the
-// blocks they hold come free in bounded time and staff it.
-__device__ void claim_slot(const QueueEntry* entries, const QueueCtl* ctl,
-                           unsigned long long* head, int* kstatus,
-                           unsigned long long idle_limit_ns, long long* slot_out,
-                           int* entry_out) {
-  const unsigned long long t_start = globaltimer();
-  unsigned polls = 0;
-  for (;;) {
-    const unsigned long long tail = ld_acquire_sys_u64(&ctl->tail);
-    const unsigned long long h = atomicAdd(head, 0ull);
-    if (h < tail) {
-      if (atomicCAS(head, h, h + 1) != h) continue;
-      // the entry holding slot h: the last one whose first slot is <= h
-      const unsigned long long ne = ld_relaxed_sys_u64(&ctl->n_entries);
-      long long lo = 0, hi = (long long)ne;   // invariant: entry lo starts at or before h
-      while (hi - lo > 1) {
-        const long long mid = (lo + hi) >> 1;
-        const QueueEntry em = load_entry(entries + mid);
-        if ((unsigned long long)em.slot0 <= h) lo = mid;
-        else hi = mid;
-      }
-      *slot_out = (long long)h;
-      *entry_out = (int)lo;
-      return;
-    }
-    if (ld_acquire_sys_u64(&ctl->stop) != 0) break;
-    if ((++polls & 63u) == 0 && globaltimer() - t_start > idle_limit_ns) {
-      atomicOr(kstatus, (int)kStatusIdleTimeout);
-      break;
-    }
-    __nanosleep(1024);
-  }
-  *slot_out = -1;
-  *entry_out = -1;
-}
-
-// Solve results for the host, read at L2 (the team's first block published
-// them), the done flag last (release at system scope).
-__device__ void write_result(const SolveState* st, PairResult* out) {
-  for (int i = 0; i < 16; ++i) out->P[i] = __ldcg(&st->P[i]);
-  out->F = __ldcg(&st->F);
-  out->t = __ldcg(&st->t);
-  out->ell = __ldcg(&st->ell);
-  out->device_ms = (double)(__ldcg(&st->t_end_ns) - __ldcg(&st->t_begin_ns)) * 1e-6;
-  out->pair_evals = (long long)__ldcg(&st->nnz_total);
-  out->candidates = (long long)__ldcg(&st->cand_total);
-  out->iters = __ldcg(&st->iter);
-  out->converged = __ldcg(&st->converged);
-  out->fallback_steps = __ldcg(&st->fallback_steps);
-  out->no_ascent_steps = __ldcg(&st->no_ascent_steps);
-  out->status = __ldcg(&st->status);
-  __threadfence_system();
-  st_release_sys_s32(&out->done, 1);
-}
-
-// Many pairs in one persistent cooperative launch. Blocks claim slots of a
-// queue of entries; the blocks holding the slots of one entry form its team.
-template <int DP, int MODE>
-__global__ void __launch_bounds__(kThreads, CVO_SOLVE_MIN_BLOCKS)
-queue_kernel(const QueueEntry* __restrict__ entries, const QueueCtl* __restrict__ ctl,
-             unsigned long long* __restrict__ head, int* __restrict__ kstatus,
-             unsigned long long idle_limit_ns, int cache_slots) {
-  constexpr int DPS = DP > 0 ? DP : 1;
-  constexpr int NU = 4;
-  __shared__ SolveSmem<DPS, NU> sm;
-  extern __shared__ float4 dyn_smem[];
-  for (;;) {
-    if (threadIdx.x == 0) {
-      long long slot;
-      int e;
-      claim_slot(entries, ctl, head, kstatus, idle_limit_ns, &slot, &e);
-      sm.q_slot = slot;
-      sm.q_entry = e;
-    }
-    __syncthreads();
-    if (sm.q_slot < 0) break;
-    const QueueEntry en = load_entry(entries + sm.q_entry);
-    const Team team{(int)(sm.q_slot - en.slot0), en.team};
-    solve_pair<DP, MODE, DPS, NU>(en.cfg, en.st, en.partials, nullptr, team, sm, true,
-                                  reinterpret_cast<float*>(dyn_smem), cache_slots);
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned left = atomicAdd(&en.st->leave_count, 1u);
-      if (left == (unsigned)en.team - 1 && en.out) {
-        __threadfence();
-        write_result(en.st, en.out);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Dynamic shared memory of the plan cache: what CVO_SOLVE_MIN_BLOCKS blocks
-// per SM leave of the SM's shared memory after their static shared memory,
-// in whole warp shares of slots (set once per kernel instantiation).
-struct CacheCfg {
-  int bytes = 0, slots = 0;
-  cudaError_t err = cudaSuccess;
-};
-
-template <int DP, int MODE>
-const CacheCfg& cache_cfg() {
-  static const CacheCfg cfg = [] {
-    CacheCfg c;
-    int dev = 0, smem_sm = 0, reserved = 0;
-    cudaFuncAttributes fa{};
-    c.err = cudaGetDevice(&dev);
-    if (c.err == cudaSuccess)
-      c.err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (c.err == cudaSuccess)
-      c.err = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (c.err == cudaSuccess) c.err = cudaFuncGetAttributes(&fa, solve_kernel<DP, MODE>);
-    if (c.err != cudaSuccess) return c;
-    const int slot_bytes = 4 * 32 * (4 + DP);
-    const int avail = smem_sm / CVO_SOLVE_MIN_BLOCKS - reserved - (int)fa.sharedSizeBytes;
-    c.slots = std::max(0, std::min(kCacheSlots, avail / (kWarps * slot_bytes)));
-    c.bytes = c.slots * kWarps * slot_bytes;
-    if (c.bytes > 0) {
-      c.err = cudaFuncSetAttribute(solve_kernel<DP, MODE>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, c.bytes);
-      if (c.err == cudaSuccess)
-        c.err = cudaFuncSetAttribute(queue_kernel<DP, MODE>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, c.bytes);
-    }
-    return c;
-  }();
-  return cfg;
-}
-
-template <int DP, int MODE>
-cudaError_t launch_solve_t(int nblocks, const SolveCfg* cfg, SolveState* st, double* partials,
-                           IterRecord* records, cudaStream_t s) {
-  const CacheCfg& cc = cache_cfg<DP, MODE>();
-  if (cc.err != cudaSuccess) return cc.err;
-  int slots = cc.slots;
-  void* args[] = {(void*)&cfg, (void*)&st, (void*)&partials, (void*)&records, (void*)&slots};
-  return cudaLaunchCooperativeKernel((const void*)solve_kernel<DP, MODE>, dim3(nblocks),
-                                     dim3(kThreads), args, (size_t)cc.bytes, s);
-}
-
-template <int DP, int MODE>
-cudaError_t launch_queue_t(int nblocks, const QueueEntry* entries, const QueueCtl* ctl,
-                           unsigned long long* head, int* kstatus, unsigned long long idle_ns,
-                           cudaStream_t s) {
-  const CacheCfg& cc = cache_cfg<DP, MODE>();
-  if (cc.err != cudaSuccess) return cc.err;
-  int slots = cc.slots;
-  void* args[] = {(void*)&entries, (void*)&ctl,     (void*)&head,
-                  (void*)&kstatus, (void*)&idle_ns, (void*)&slots};
-  return cudaLaunchCooperativeKernel((const void*)queue_kernel<DP, MODE>, dim3(nblocks),
-                                     dim3(kThreads), args, (size_t)cc.bytes, s);
-}
-
-template <int DP, int MODE>
-int blocks_per_sm_t() {
-  const CacheCfg& cc = cache_cfg<DP, MODE>();
-  if (cc.err != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_kernel<DP, MODE>, kThreads,
-                                                    (size_t)cc.bytes) != cudaSuccess)
-    return 0;
-  return n;
-}
-
-}  // namespace
+#define CVO_DECLARE_DP(D)                                                                    \
+  cudaError_t launch_solve_d##D(int color_mode, int nblocks, const SolveCfg* cfg,            \
+                                SolveState* st, double* partials, IterRecord* records,       \
+                                cudaStream_t s);                                             \
+  cudaError_t launch_queue_d##D(int color_mode, int nblocks, const QueueEntry* entries,      \
+                                const QueueCtl* ctl, unsigned long long* head, int* kstatus, \
+                                unsigned long long idle_limit_ns, cudaStream_t s);           \
+  int blocks_per_sm_d##D(int color_mode);
+CVO_DECLARE_DP(0)
+CVO_DECLARE_DP(3)
+CVO_DECLARE_DP(5)
+CVO_DECLARE_DP(8)
+#undef CVO_DECLARE_DP
 
 cudaError_t launch_solve(int dp, int color_mode, int nblocks, const SolveCfg* cfg, SolveState* st,
                          double* partials, IterRecord* records, cudaStream_t s) {
-  if (color_mode == kColorNone || dp == 0)
-    return launch_solve_t<0, kColorNone>(nblocks, cfg, st, partials, records, s);
-  if (color_mode == kColorKernel) {
-    if (dp == 3) return launch_solve_t<3, kColorKernel>(nblocks, cfg, st, partials, records, s);
-    if (dp == 5) return launch_solve_t<5, kColorKernel>(nblocks, cfg, st, partials, records, s);
-    return launch_solve_t<8, kColorKernel>(nblocks, cfg, st, partials, records, s);
-  }
-  if (dp == 3) return launch_solve_t<3, kColorDot>(nblocks, cfg, st, partials, records, s);
-  if (dp == 5) return launch_solve_t<5, kColorDot>(nblocks, cfg, st, partials, records, s);
-  return launch_solve_t<8, kColorDot>(nblocks, cfg, st, partials, records, s);
+  if (color_of(color_mode) == kColorNone || dp == 0)
+    return launch_solve_d0(kColorNone, nblocks, cfg, st, partials, records, s);
+  if (dp == 3) return launch_solve_d3(color_mode, nblocks, cfg, st, partials, records, s);
+  if (dp == 5) return launch_solve_d5(color_mode, nblocks, cfg, st, partials, records, s);
+  return launch_solve_d8(color_mode, nblocks, cfg, st, partials, records, s);
 }
 
 cudaError_t launch_queue(int dp, int color_mode, int nblocks, const QueueEntry* entries,
                          const QueueCtl* ctl, unsigned long long* head, int* kstatus,
                          unsigned long long idle_limit_ns, cudaStream_t s) {
-  if (color_mode == kColorNone || dp == 0)
-    return launch_queue_t<0, kColorNone>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
-  if (color_mode == kColorKernel) {
-    if (dp == 3)
-      return launch_queue_t<3, kColorKernel>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
-    if (dp == 5)
-      return launch_queue_t<5, kColorKernel>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
-    return launch_queue_t<8, kColorKernel>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
-  }
+  if (color_of(color_mode) == kColorNone || dp == 0)
+    return launch_queue_d0(kColorNone, nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
   if (dp == 3)
-    return launch_queue_t<3, kColorDot>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+    return launch_queue_d3(color_mode, nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
   if (dp == 5)
-    return launch_queue_t<5, kColorDot>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
-  return launch_queue_t<8, kColorDot>(nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+    return launch_queue_d5(color_mode, nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
+  return launch_queue_d8(color_mode, nblocks, entries, ctl, head, kstatus, idle_limit_ns, s);
 }
 
 int solve_blocks_per_sm(int dp, int color_mode) {
-  if (color_mode == kColorNone || dp == 0) return blocks_per_sm_t<0, kColorNone>();
-  if (color_mode == kColorKernel) {
-    if (dp == 3) return blocks_per_sm_t<3, kColorKernel>();
-    if (dp == 5) return blocks_per_sm_t<5, kColorKernel>();
-    return blocks_per_sm_t<8, kColorKernel>();
-  }
-  if (dp == 3) return blocks_per_sm_t<3, kColorDot>();
-  if (dp == 5) return blocks_per_sm_t<5, kColorDot>();
-  return blocks_per_sm_t<8, kColorDot>();
+  if (color_of(color_mode) == kColorNone || dp == 0) return blocks_per_sm_d0(kColorNone);
+  if (dp == 3) return blocks_per_sm_d3(color_mode);
+  if (dp == 5) return blocks_per_sm_d5(color_mode);
+  return blocks_per_sm_d8(color_mode);
 }
 
 }  // namespace cvo

@@ -40,6 +40,7 @@ struct Cloud {
   int64_t n = 0;
   int n_pad = 0;
   int D = 0, dp = 0;
+  int fbytes = 4;         // bytes per stored feature value: 4 (FP32) or 2 (BF16)
   double c[3] = {0, 0, 0};
   float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // bounding box, centred frame
   MortonFrame mf{};
@@ -152,6 +153,7 @@ double pair_work(const cvo_params& prm, const Cloud* t, const Cloud* s,
 void fill_stats(const SolveState* hs, cvo_stats* stats);
 int status_code(int bits);
 int check_pose(cvo_ctx* ctx, const double* P);
+int kernel_mode(const cvo_params& p);   // label product | kFeatBf16
 
 // serve.cu
 void serve_shutdown(cvo_ctx* ctx);   // drain and stop the request loop (no lock held)

@@ -38,7 +38,6 @@ namespace cvo {
 namespace {
 
 constexpr int kEntryCap = 16384;                       // entries per kernel epoch
-constexpr unsigned long long kIdleLimitNs = 10ull * 1000 * 1000 * 1000;   // kernel-side bound
 
 double now_ms() {
   return std::chrono::duration<double, std::milli>(
@@ -93,6 +92,10 @@ struct Serve {
   unsigned long long* d_head = nullptr;   // slot counter, then the kernel status word
   int n_entries = 0;
   unsigned long long tail = 0;
+  int* h_kstatus = nullptr;               // pinned: the last kernel's status word
+  // counters (stats_mu)
+  std::mutex stats_mu;
+  cvo_serve_stats stats{};
 };
 
 namespace {
@@ -131,6 +134,11 @@ void finish(cvo_ctx* ctx, Serve* sv, Req* r, int code) {
   r->feat.clear();
   r->feat.shrink_to_fit();
   if (Cloud* t_cloud = get_cloud(ctx, r->target)) t_cloud->refs -= 1;
+  {
+    std::lock_guard<std::mutex> lk(sv->stats_mu);
+    sv->stats.completed += 1;
+    if (out.stats.status != CVO_OK) sv->stats.failed += 1;
+  }
   std::lock_guard<std::mutex> lk(sv->mu);
   r->done = true;
 }
@@ -172,9 +180,16 @@ int prepare(cvo_ctx* ctx, Serve* sv, Req* r) {
 
 int launch_epoch(cvo_ctx* ctx, Serve* sv) {
   CK(cudaMemsetAsync(sv->d_head, 0, 2 * sizeof(unsigned long long), sv->stream));
+  const unsigned long long idle_ns = (unsigned long long)(sv->prm.idle_limit_ms * 1e6);
   CK(launch_queue(sv->dp, sv->color_mode, sv->nblocks, sv->d_entries, sv->d_ctl, sv->d_head,
-                  reinterpret_cast<int*>(sv->d_head + 1), kIdleLimitNs, sv->stream));
+                  reinterpret_cast<int*>(sv->d_head + 1), idle_ns, sv->stream));
+  CK(cudaMemcpyAsync(sv->h_kstatus, sv->d_head + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                     sv->stream));
   CK(cudaEventRecord(sv->epoch_done, sv->stream));
+  {
+    std::lock_guard<std::mutex> lk(sv->stats_mu);
+    sv->stats.kernels_launched += 1;
+  }
   sv->epoch = true;
   sv->stopping = false;
   sv->idle_since = -1.0;
@@ -244,6 +259,10 @@ void collect(cvo_ctx* ctx, Serve* sv) {
     sv->epoch = false;
     sv->stopping = false;
     sv->inflight_work = 0.0;
+    if (kernel_err == CVO_OK && (*sv->h_kstatus & kStatusIdleTimeout)) {
+      std::lock_guard<std::mutex> lk(sv->stats_mu);
+      sv->stats.idle_exits += 1;
+    }
   }
 }
 
@@ -328,6 +347,8 @@ void release_device(Serve* sv) {
   if (sv->h_entries) cudaFreeHost(sv->h_entries);
   if (sv->h_results) cudaFreeHost(sv->h_results);
   if (sv->h_ctl) cudaFreeHost(sv->h_ctl);
+  if (sv->h_kstatus) cudaFreeHost(sv->h_kstatus);
+  sv->h_kstatus = nullptr;
   if (sv->d_head) cudaFree(sv->d_head);
   sv->epoch_done = nullptr;
   sv->stream = nullptr;
@@ -348,18 +369,19 @@ int start_locked(cvo_ctx* ctx, const cvo_serve_params& prm) {
     if (p.color_mode == CVO_COLOR_NONE || p.feat_dim == 0) return 0;
     return p.feat_dim <= 3 ? 3 : p.feat_dim <= 5 ? 5 : 8;
   }();
-  const int per_sm = solve_blocks_per_sm(dp, ctx->prm.color_mode);
+  const int per_sm = solve_blocks_per_sm(dp, kernel_mode(ctx->prm));
   if (per_sm <= 0) return fail(ctx, CVO_ERR_CUDA, "solve kernel cannot be resident");
   // block slots left free: the frame preparation kernels (at most 32K
   // registers and 1024 threads a block, the size of one solve block) must find
   // room while the serving kernel holds every other slot
   const int slots = std::min(per_sm * ctx->sms, 512);
   if (prm.reserve_blocks < 1 || prm.reserve_blocks >= slots || prm.max_inflight < 1 ||
-      prm.max_inflight > 65536 || !(prm.linger_ms >= 0.0) || !std::isfinite(prm.linger_ms))
+      prm.max_inflight > 65536 || !(prm.linger_ms >= 0.0) || !std::isfinite(prm.linger_ms) ||
+      !(prm.idle_limit_ms > 0.0) || !(prm.idle_limit_ms <= 3.6e6))
     return fail(ctx, CVO_ERR_INVALID_ARG, "bad serve parameters");
   sv->prm = prm;
   sv->dp = dp;
-  sv->color_mode = ctx->prm.color_mode;
+  sv->color_mode = kernel_mode(ctx->prm);
   sv->nblocks = slots - prm.reserve_blocks;
   if (!sv->h_entries) {
     cudaError_t e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
@@ -374,6 +396,7 @@ int start_locked(cvo_ctx* ctx, const cvo_serve_params& prm) {
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sv->d_results, sv->h_results, 0);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sv->d_ctl, sv->h_ctl, 0);
     if (e == cudaSuccess) e = cudaMalloc((void**)&sv->d_head, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&sv->h_kstatus, sizeof(int));
     if (e != cudaSuccess) {
       release_device(sv);
       return fail(ctx, CVO_ERR_CUDA, std::string("request loop setup: ") + cudaGetErrorString(e));
@@ -423,6 +446,7 @@ void cvo_serve_params_default(cvo_serve_params* p) {
   p->reserve_blocks = 8;
   p->max_inflight = 1024;
   p->linger_ms = 0.5;
+  p->idle_limit_ms = 10000.0;
 }
 
 int cvo_serve_start(cvo_ctx* ctx, const cvo_serve_params* params) {
@@ -487,6 +511,10 @@ int cvo_submit(cvo_ctx* ctx, const cvo_request* req, uint64_t* ticket) {
     std::lock_guard<std::mutex> lk(sv->mu);
     r->ticket = sv->next_ticket++;
     sv->tickets[r->ticket] = r;
+    {
+      std::lock_guard<std::mutex> lk2(sv->stats_mu);
+      sv->stats.submitted += 1;
+    }
     sv->pending.push_back(r);
     sv->pending_work += r->work;
     *ticket = r->ticket;
@@ -525,6 +553,16 @@ int cvo_serve_stop(cvo_ctx* ctx) {
   }
   sv->cv.notify_all();
   if (sv->th.joinable()) sv->th.join();
+  return CVO_OK;
+}
+
+int cvo_serve_get_stats(cvo_ctx* ctx, cvo_serve_stats* out) {
+  if (!ctx || !out) return CVO_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  Serve* sv = ctx->serve;
+  if (!sv) return CVO_OK;
+  std::lock_guard<std::mutex> lk(sv->stats_mu);
+  *out = sv->stats;
   return CVO_OK;
 }
 

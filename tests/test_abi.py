@@ -66,7 +66,8 @@ def test_struct_layouts_match_the_header(lib_path):
     (checked by compiling a tiny C program against the header)."""
     import paper_1904_02266_gb300 as cvo
     structs = [cvo.cvo_params, cvo.cvo_eval_result, cvo.cvo_stats, cvo.cvo_iter_profile,
-               cvo.cvo_batch_info, cvo.cvo_request, cvo.cvo_result, cvo.cvo_serve_params]
+               cvo.cvo_batch_info, cvo.cvo_request, cvo.cvo_result, cvo.cvo_serve_params,
+               cvo.cvo_serve_stats]
     lines = []
     for st in structs:
         name = st.__name__

@@ -91,6 +91,49 @@ def test_eval_planes(cvo, mode, ell):
             _check_eval(g, d["X"], FX, d["Z"], FZ, P, ell, prm, f"{mode} {ell}")
 
 
+def _bf16_stored(F, scale):
+    """The features the library keeps in BF16 mode: the FP32 product f * scale
+    rounded to BF16 (nearest, ties to even), expressed back in feature units."""
+    x = (np.asarray(F, dtype=np.float32) * np.float32(scale)).astype(np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64) / float(np.float32(scale))
+
+
+@pytest.mark.parametrize("mode", ["kernel", "dot"])
+def test_eval_bf16_features(cvo, mode):
+    # BF16 storage: the oracle is given the features as stored, so only the
+    # FP32 pair arithmetic separates the two sides
+    d = synth.planes_pair(1500, 1300, seed=synth.seed_for(1, 21))
+    kw = {"feat_bf16": 1, "color_mode": 1 if mode == "kernel" else 2}
+    if mode == "dot":
+        kw["color_scale"] = 1.0
+    with _ctx(cvo, **kw) as ctx:
+        prm = _oracle_params(ctx.params, cvo)
+        scale = (np.sqrt(1.4426950408889634 / (2.0 * ctx.params.ell_color ** 2)) if mode == "kernel"
+                 else np.sqrt(ctx.params.color_scale))
+        FXs, FZs = _bf16_stored(d["FX"], scale), _bf16_stored(d["FZ"], scale)
+        assert not np.array_equal(FXs, d["FX"].astype(np.float64))   # rounding did happen
+        ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+        for P, ell in [(np.eye(4), 0.1), (d["P_gt"], 0.05)]:
+            g = ctx.eval(ht, hs, P, ell)
+            _check_eval(g, d["X"], FXs, d["Z"], FZs, P, ell, prm, f"bf16 {mode} {ell}")
+
+
+def test_align_bf16_features(cvo):
+    d = synth.planes_pair(1500, 1500, seed=synth.seed_for(1, 22))
+    with _ctx(cvo, feat_bf16=1) as ctx:
+        prm = _oracle_params(ctx.params, cvo)
+        scale = np.sqrt(1.4426950408889634 / (2.0 * ctx.params.ell_color ** 2))
+        ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+        P_gpu, st = ctx.align(ht, hs)
+    FXs, FZs = _bf16_stored(d["FX"], scale), _bf16_stored(d["FZ"], scale)
+    res = oracle.align(d["X"], FXs, d["Z"], FZs, np.eye(4), prm)
+    ang, tr = oracle.pose_error(P_gpu, res["P"])
+    assert ang <= POSE_TOL and tr <= POSE_TOL, (ang, tr)
+    assert abs(st["iters"] - res["iters"]) <= 3
+
+
 @pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 7, 8])
 def test_feature_dims(cvo, D):
     rng = np.random.default_rng(100 + D)
@@ -292,6 +335,33 @@ def test_eval_room_full_size(cvo):
         for P, ell in [(np.eye(4), 0.15), (d["P_gt"], 0.02), (np.eye(4), 0.05)]:
             g = ctx.eval(ht, hs, P, ell)
             _check_eval(g, d["X"], d["FX"], d["Z"], d["FZ"], P, ell, prm, f"room {ell}")
+
+
+@pytest.mark.slow
+def test_eval_dense_room_100k(cvo):
+    """The dense precision-sweep size: N = M = 100,000 points (room frames,
+    95% of the valid pixels kept, subsampled), F, gradient and step sums at a
+    fixed pose against the exhaustive FP64 oracle (10^10 pair tests a pass)."""
+    d = synth.room_pair(n_points=100000, seed=synth.seed_for(4), mode="valid")
+    with _ctx(cvo) as ctx:
+        prm = _oracle_params(ctx.params, cvo)
+        ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+        g = ctx.eval(ht, hs, np.eye(4), 0.05)
+        _check_eval(g, d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4), 0.05, prm, "room 100k")
+
+
+def test_fp32_reduction_mode_is_looser_but_close(cvo):
+    # precision study: FP32 block and cross-block sums against the FP64 oracle
+    d = synth.room_pair()
+    with _ctx(cvo, reduce_fp32=1) as ctx:
+        prm = _oracle_params(ctx.params, cvo)
+        ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+        g = ctx.eval(ht, hs, np.eye(4), 0.05)
+    r = oracle.pair_sums(d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4), 0.05, prm)
+    ref = oracle.gradient(r, prm)
+    assert abs(g["F"] - r["F"]) <= 1e-4 * abs(r["F"])
+    assert np.linalg.norm(g["grad6"] - ref) <= 1e-3 * np.linalg.norm(ref)
+    assert g["nnz"] == pytest.approx(r["nnz"], abs=max(2, 1e-6 * r["nnz"]))
 
 
 @pytest.mark.slow

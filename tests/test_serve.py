@@ -150,3 +150,26 @@ def test_busy_rules_and_tickets(cvo):
         ang, tr = oracle.pose_error(P, r[0])
         assert ang < POSE_TOL and tr < POSE_TOL
         ctx.release(k)
+
+
+def test_idle_bound_of_the_serving_kernel(cvo):
+    """A bounded device wait that runs out: the loop never tells the serving
+    kernel to leave (linger far beyond the test), so the kernel's own idle
+    bound ends it; the host reads the status, counts the exit, and the next
+    request starts a new kernel and completes."""
+    d = synth.planes_pair(1200, 1000, seed=synth.seed_for(5, 50))
+    with cvo.Context(device=0) as ctx:
+        k = ctx.set_cloud(d["X"], d["FX"])
+        ctx.serve_start(linger_ms=1e6, idle_limit_ms=50.0)
+        r1 = _wait_all(ctx, [ctx.submit(k, d["Z"], d["FZ"])])[0]
+        t_end = time.time() + 20.0
+        while ctx.serve_stats()["idle_exits"] < 1:
+            assert time.time() < t_end, "the serving kernel did not leave on its idle bound"
+            time.sleep(0.01)
+        r2 = _wait_all(ctx, [ctx.submit(k, d["Z"], d["FZ"])])[0]
+        st = ctx.serve_stats()
+        assert r1[1]["status"] == 0 and r2[1]["status"] == 0
+        assert st["kernels_launched"] == 2 and st["idle_exits"] >= 1
+        assert st["submitted"] == 2 and st["completed"] == 2 and st["failed"] == 0
+        ang, tr = oracle.pose_error(r1[0], r2[0])
+        assert ang < POSE_TOL and tr < POSE_TOL
