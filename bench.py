@@ -82,6 +82,10 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--odometry", action="store_true",
+                    help="instead of the benchmark line, print odometry over a rendered trajectory")
+    ap.add_argument("--order-study", action="store_true",
+                    help="instead of the benchmark line, print the 2nd- vs 4th-order step study")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="instead of the benchmark line, print the dense precision sweep "
                          "(100k points: FP64 reductions vs FP32 reductions vs BF16 features)")
@@ -545,6 +549,105 @@ def precision_sweep():
     print(json.dumps({"precision_sweep": out}), flush=True)
 
 
+def odometry(n_frames=30):
+    """Odometry over a stream (Sec. 5 protocol on a synthetic trajectory): 30
+    VGA frames of a camera moving through the procedural room (3 deg / 3 cm
+    seeded steps, 20,000 points per frame); every consecutive pair is solved,
+    all in one batch and one at a time, and scored with the Sec. 2 distances
+    (relative rotation angle and translation error, their percentiles, and the
+    drift of the chained trajectory). Three pairs are checked against the FP64
+    oracle's solve."""
+    import oracle
+    import torch
+    import paper_1904_02266_gb300 as cvo
+    from paper_1904_02266_gb300 import build as cvo_build
+    cvo_build.build()
+    t0 = time.time()
+    tr = synth.room_trajectory(n_frames=n_frames, n_points=N_POINTS)
+    gen_s = time.time() - t0
+    fr = tr["frames"]
+    n = len(fr) - 1
+    with cvo.Context(device=0) as ctx:
+        h = [ctx.set_cloud(X, F) for X, F in fr]
+        stream = torch.cuda.ExternalStream(ctx.stream)
+        with ctx.batch(h[:-1], h[1:]) as b:
+            b.run(np.stack([np.eye(4)] * n))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P, st = b.run(np.stack([np.eye(4)] * n))
+            e1.record(stream)
+            e1.synchronize()
+            batch_ms = e0.elapsed_time(e1)
+        plain_ms = 0.0
+        for k in range(n):
+            ctx.align(h[k], h[k + 1])
+            e0.record(stream)
+            ctx.align(h[k], h[k + 1])
+            e1.record(stream)
+            e1.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+    rot = np.array([synth_pose_err(P[k], tr["P_gt"][k])[0] for k in range(n)])
+    trans = np.array([synth_pose_err(P[k], tr["P_gt"][k])[1] for k in range(n)])
+    T = np.eye(4)
+    for k in range(n):
+        T = T @ P[k]
+    T_gt = np.linalg.inv(tr["T_wc"][0]) @ tr["T_wc"][-1]
+    prm = oracle.Params()
+    worst = 0.0
+    for k in (0, n // 2, n - 1):
+        ref = oracle.align(fr[k][0], fr[k][1], fr[k + 1][0], fr[k + 1][1], np.eye(4), prm)
+        worst = max(worst, *synth_pose_err(P[k], ref["P"]))
+
+    def pct(a):
+        return {q: float(np.percentile(a, q)) for q in (50, 90, 100)}
+
+    out = {"workload": f"{n_frames} VGA frames of a rendered room trajectory, 3 deg / 3 cm steps, "
+                       f"{N_POINTS} points per frame", "pairs": n, "render_s": gen_s,
+           "rpe_rot_deg": {k: np.rad2deg(v) for k, v in pct(rot).items()},
+           "rpe_trans_cm": {k: 100 * v for k, v in pct(trans).items()},
+           "drift_end": {"rot_deg": float(np.rad2deg(synth_pose_err(T, T_gt)[0])),
+                         "trans_cm": 100 * synth_pose_err(T, T_gt)[1],
+                         "path_m": float(sum(np.linalg.norm(M[:3, 3]) for M in tr["P_gt"]))},
+           "batch_ms": batch_ms, "batch_frame_pairs_per_s": n / (batch_ms * 1e-3),
+           "plain_ms": plain_ms, "plain_frame_pairs_per_s": n / (plain_ms * 1e-3),
+           "max_pose_diff_vs_oracle_3_pairs": worst,
+           "converged": int(sum(x["converged"] for x in st)), "iters_median": float(
+               np.median([x["iters"] for x in st]))}
+    print(json.dumps({"odometry": out}), flush=True)
+
+
+def order_study():
+    """Step rule of Sec. 4: the quadratic (2nd-order, t = -S1 / 2 S2) against the
+    quartic (4th-order, first maximiser) Taylor model, on the planes pair
+    (config 1) and the room pair (config 2): iterations, convergence, fallback
+    steps, solve time, and the final pose against the truth and against the
+    FP64 oracle's solve with the same rule."""
+    import oracle
+    import paper_1904_02266_gb300 as cvo
+    from paper_1904_02266_gb300 import build as cvo_build
+    cvo_build.build()
+    cases = {"planes_2k": synth.planes_pair(), "room_20k": synth.room_pair()}
+    out = {}
+    for cname, d in cases.items():
+        for order in (2, 4):
+            with cvo.Context(device=0, step_order=order) as ctx:
+                ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+                ctx.align(ht, hs)
+                t0 = time.perf_counter()
+                P, st = ctx.align(ht, hs)
+                dt = time.perf_counter() - t0
+                prm = oracle.Params()
+                prm.step_order = order
+                ref = oracle.align(d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4), prm)
+            out[f"{cname}_order{order}"] = {
+                "iters": st["iters"], "converged": st["converged"],
+                "fallback_steps": st["fallback_steps"], "solve_ms": dt * 1e3,
+                "pose_vs_truth": list(synth_pose_err(P, d["P_gt"])),
+                "pose_vs_oracle": list(synth_pose_err(P, ref["P"])),
+                "oracle_iters": ref["iters"]}
+    print(json.dumps({"order_study": out}), flush=True)
+
+
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
     summary was taken on the current kernel source (else None)."""
@@ -576,9 +679,14 @@ def synth_pose_err(P, Pref):
 def main():
     args = parse_args()
     world, rank, local = dist_env()
-    if args.precision_sweep:
+    if args.precision_sweep or args.order_study or args.odometry:
         if rank == 0:
-            precision_sweep()
+            if args.odometry:
+                odometry()
+            if args.order_study:
+                order_study()
+            if args.precision_sweep:
+                precision_sweep()
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

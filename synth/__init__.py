@@ -347,3 +347,49 @@ def serving_trace(n_streams=64, rate_hz=30.0, duration_s=20.0, n_range=(5000, 60
             t += float(rng.exponential(1.0 / rate_hz))
     out.sort(key=lambda r: r["t"])
     return out
+
+
+# --------------------------------------------------------------------------
+# odometry over a stream: a camera trajectory through one room
+# --------------------------------------------------------------------------
+
+def room_trajectory(n_frames=30, n_points=20000, seed=None, step_deg=3.0, step_m=0.03,
+                    width=640, height=480, mode="gradient"):
+    """Frames of one camera moving through a procedural room: each step is a
+    seeded motion of step_deg / step_m (as between the two frames of
+    room_pair). Returns frames (X_k, F_k) in their own camera frames, the
+    camera-to-world poses T_wc_k, and the relative poses P_gt_k that map frame
+    k+1's coordinates into frame k (the pose the solver estimates with frame k
+    as target and frame k+1 as source)."""
+    seed = seed_for(6) if seed is None else seed
+    rng = np.random.default_rng(seed)
+    cam = np.array([rng.uniform(0.8, 1.2), rng.uniform(2.0, 3.0), rng.uniform(1.2, 1.6)])
+    room = Room(rng, keep_clear=cam)
+    T = rigid(_camera_rotation(rng.uniform(-0.35, 0.35), rng.uniform(-0.25, -0.05)), cam)
+    poses, frames, rel = [T], [], []
+    for k in range(n_frames - 1):
+        M = random_motion(rng, step_deg, step_m)
+        rel.append(M)
+        T = T @ M
+        poses.append(T)
+    for T_wc in poses:
+        p, c, v = render(room, T_wc, rng, width, height)
+        X, F = select_points(p, c, v, rng, n_points, mode)
+        frames.append((X.astype(np.float32), F.astype(np.float32)))
+    return {"frames": frames, "T_wc": poses, "P_gt": rel, "seed": seed}
+
+
+def room_frame_images(seed=None, width=640, height=480):
+    """One rendered RGB-D frame as images: depth (H, W) float32 (0 where
+    invalid: no hit, or outside 0.5-5 m), HSV colour (H, W, 3) float32, and
+    the pinhole intrinsics (fx, fy, cx, cy) of render."""
+    seed = seed_for(7) if seed is None else seed
+    rng = np.random.default_rng(seed)
+    cam = np.array([rng.uniform(0.6, 1.0), rng.uniform(2.0, 3.0), rng.uniform(1.2, 1.6)])
+    room = Room(rng, keep_clear=cam)
+    T_wc = rigid(_camera_rotation(rng.uniform(-0.35, 0.35), rng.uniform(-0.25, -0.05)), cam)
+    fx = fy = 525.0 * width / 640.0
+    cx, cy = (width - 1) / 2.0, (height - 1) / 2.0
+    p, c, v = render(room, T_wc, rng, width, height, fx, fy, cx, cy)
+    depth = np.where(v, p[..., 2], 0.0).astype(np.float32)
+    return {"depth": depth, "hsv": c.astype(np.float32), "fx": fx, "fy": fy, "cx": cx, "cy": cy}

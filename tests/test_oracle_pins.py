@@ -385,3 +385,18 @@ def test_scale_parameters_only_scale(oracle_mod):
     for r in (r1, r2):
         ang, tr = oracle_mod.pose_error(r["P"], r0["P"])
         assert ang < 1e-10 and tr < 1e-10
+
+
+def test_trajectory_ground_truth_composes():
+    # the relative poses the odometry test scores against chain to the
+    # absolute camera poses: T_wc[k+1] = T_wc[k] P_gt[k]
+    tr = synth.room_trajectory(n_frames=4, n_points=300, width=96, height=72,
+                               seed=synth.seed_for(6, 2))
+    for k in range(3):
+        assert np.allclose(tr["T_wc"][k + 1], tr["T_wc"][k] @ tr["P_gt"][k], atol=1e-12)
+    # a frame's points seen from the next camera: x_k = P_gt[k] x_{k+1} for a
+    # static world point (checked on a synthetic point, not the sampled ones)
+    w = np.array([1.5, 2.0, 0.7, 1.0])
+    xk = np.linalg.inv(tr["T_wc"][0]) @ w
+    xk1 = np.linalg.inv(tr["T_wc"][1]) @ w
+    assert np.allclose(tr["P_gt"][0] @ xk1, xk, atol=1e-12)
