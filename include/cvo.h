@@ -329,6 +329,48 @@ int cvo_serve_stop(cvo_ctx* ctx);
  * (zeros if it never ran). */
 int cvo_serve_get_stats(cvo_ctx* ctx, cvo_serve_stats* out);
 
+/* ---- semi-dense front end (Sec. 5: high intensity-gradient pixels) -------- */
+
+typedef struct {
+    double fx, fy, cx, cy;        /* pinhole intrinsics [pixels]; 525, 525, 319.5, 239.5 */
+    double depth_min, depth_max;  /* a pixel is valid if its depth [m] lies in this range; 0.5, 5 */
+    double percentile;            /* keep the valid pixels whose intensity-gradient magnitude is
+                                     above this percentile of the valid pixels' magnitudes
+                                     (linear interpolation between order statistics); 80 */
+    double grad_scale;            /* gradient features are clip(g / grad_scale, -1, 1); 0.05 */
+    int64_t max_points;           /* when more pixels are kept, keep the ranks
+                                     floor(k m / max_points) of the m kept pixels (raster order);
+                                     0 = keep all */
+} cvo_frontend_params;
+
+/* Fill *p with the defaults listed in cvo_frontend_params. */
+void cvo_frontend_params_default(cvo_frontend_params* p);
+
+/* Select, back-project and describe the points of one RGB-D frame on the GPU.
+ * depth is H x W float32 [m] (row-major), hsv H x W x 3 float32 (H, S, V;
+ * the intensity is V); host arrays, or device arrays with CVO_DEVICE_PTR
+ * (read on `stream`, NULL = the context stream). The intensity gradient is
+ * taken by central differences (one-sided at the image border) in FP32, its
+ * magnitude compared with the percentile threshold in FP64, and the kept
+ * pixels, in raster order, are written as points x = ((u - cx) / fx) z,
+ * y = ((v - cy) / fy) z, z = depth into out_xyz (n x 3) with features H, S,
+ * V, clip(gx / grad_scale), clip(gy / grad_scale) into out_feat (n x 5, may be
+ * NULL) and their pixel indices y W + x into out_pixel (may be NULL); all
+ * three are device arrays with room for `capacity` points. *n_out receives n.
+ * Errors: CVO_ERR_INVALID_ARG (image smaller than 2 x 2 or above 2^20 pixels,
+ * bad parameters, no valid pixel, more points than capacity). */
+int cvo_frontend_select(cvo_ctx* ctx, const float* depth, const float* hsv, int width, int height,
+                        const cvo_frontend_params* params, uint32_t flags, void* stream,
+                        float* out_xyz, float* out_feat, int32_t* out_pixel, int64_t capacity,
+                        int64_t* n_out);
+
+/* The same selection, uploaded as a resident cloud (as cvo_set_cloud does)
+ * without leaving the device. The context's feat_dim must be 5 (or features
+ * unused). *handle_out receives the cloud, *n_out (may be NULL) its size. */
+int cvo_frontend_cloud(cvo_ctx* ctx, const float* depth, const float* hsv, int width, int height,
+                       const cvo_frontend_params* params, uint32_t flags, void* stream,
+                       int32_t* handle_out, int64_t* n_out);
+
 /* Gradient pass for callers that must not allocate device memory during the
  * call: a program whose device memory is all owned by its own pool or fixed
  * at start-up (a real-time loop with a frozen footprint, an embedding host

@@ -40,7 +40,8 @@ EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
            "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile", "cvo_stream",
            "cvo_batch_create", "cvo_batch_run", "cvo_batch_get_info", "cvo_batch_destroy",
            "cvo_serve_params_default", "cvo_serve_start", "cvo_submit", "cvo_poll",
-           "cvo_serve_stop", "cvo_serve_get_stats",
+           "cvo_serve_stop", "cvo_serve_get_stats", "cvo_frontend_params_default",
+           "cvo_frontend_select", "cvo_frontend_cloud",
            "cvo_eval_gradient_static", "cvo_strerror", "cvo_last_error")
 
 
@@ -120,6 +121,13 @@ class cvo_serve_stats(ctypes.Structure):
                 ("idle_exits", ctypes.c_int64)]
 
 
+class cvo_frontend_params(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
+                ("cy", ctypes.c_double), ("depth_min", ctypes.c_double),
+                ("depth_max", ctypes.c_double), ("percentile", ctypes.c_double),
+                ("grad_scale", ctypes.c_double), ("max_points", ctypes.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -173,6 +181,15 @@ def load_library(path: str = LIB_PATH):
                                  ctypes.POINTER(ctypes.c_int)]
         lib.cvo_serve_stop.argtypes = [vp]
         lib.cvo_serve_get_stats.argtypes = [vp, ctypes.POINTER(cvo_serve_stats)]
+        fpp = ctypes.POINTER(cvo_frontend_params)
+        lib.cvo_frontend_params_default.argtypes = [fpp]
+        lib.cvo_frontend_params_default.restype = None
+        lib.cvo_frontend_select.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, fpp,
+                                            ctypes.c_uint32, vp, vp, vp, vp, ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_int64)]
+        lib.cvo_frontend_cloud.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, fpp,
+                                           ctypes.c_uint32, vp, i32p,
+                                           ctypes.POINTER(ctypes.c_int64)]
         lib.cvo_stream.argtypes = [vp]
         lib.cvo_stream.restype = ctypes.c_void_p
         lib.cvo_strerror.argtypes = [ctypes.c_int]
@@ -182,7 +199,8 @@ def load_library(path: str = LIB_PATH):
         for name in ("cvo_create", "cvo_destroy", "cvo_set_cloud", "cvo_release_cloud",
                      "cvo_eval", "cvo_align", "cvo_batch_create", "cvo_batch_run",
                      "cvo_batch_get_info", "cvo_batch_destroy", "cvo_serve_start",
-                     "cvo_submit", "cvo_poll", "cvo_serve_stop", "cvo_serve_get_stats"):
+                     "cvo_submit", "cvo_poll", "cvo_serve_stop", "cvo_serve_get_stats",
+                     "cvo_frontend_select", "cvo_frontend_cloud"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -399,6 +417,56 @@ def cvo_serve_get_stats(ctx) -> dict:
     return {k: getattr(st, k) for k, _ in cvo_serve_stats._fields_}
 
 
+def cvo_frontend_params_default(**overrides) -> cvo_frontend_params:
+    p = cvo_frontend_params()
+    load_library().cvo_frontend_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _image_args(depth, hsv, stream):
+    """Host numpy images, or CUDA tensors (device pointers, current torch stream)."""
+    keep, flags = [], 0
+    dev = hasattr(depth, "data_ptr") and getattr(depth, "is_cuda", False)
+    if dev:
+        flags |= CVO_DEVICE_PTR
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(depth.device).cuda_stream
+        return depth.data_ptr(), hsv.data_ptr(), int(depth.shape[0]), int(depth.shape[1]), \
+            flags, stream, keep
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    h = np.ascontiguousarray(hsv, dtype=np.float32)
+    keep += [d, h]
+    return d.ctypes.data, h.ctypes.data, d.shape[0], d.shape[1], flags, stream, keep
+
+
+def cvo_frontend_select(ctx, depth, hsv, params: cvo_frontend_params, out_xyz, out_feat=None,
+                        out_pixel=None, stream=None) -> int:
+    """Selection into caller device tensors (float32 (cap, 3), (cap, 5), int32
+    (cap,)); returns the number of points."""
+    dp, hp, H, W, flags, stream, keep = _image_args(depth, hsv, stream)
+    n = ctypes.c_int64(0)
+    cap = int(out_xyz.shape[0])
+    _check(ctx, load_library().cvo_frontend_select(
+        ctx, dp, hp, W, H, ctypes.byref(params), flags, stream if stream else None,
+        out_xyz.data_ptr(), None if out_feat is None else out_feat.data_ptr(),
+        None if out_pixel is None else out_pixel.data_ptr(), cap, ctypes.byref(n)))
+    return int(n.value)
+
+
+def cvo_frontend_cloud(ctx, depth, hsv, params: cvo_frontend_params, stream=None):
+    """The selection as a resident cloud: (handle, number of points)."""
+    dp, hp, H, W, flags, stream, keep = _image_args(depth, hsv, stream)
+    h = ctypes.c_int32(-1)
+    n = ctypes.c_int64(0)
+    _check(ctx, load_library().cvo_frontend_cloud(ctx, dp, hp, W, H, ctypes.byref(params), flags,
+                                                  stream if stream else None, ctypes.byref(h),
+                                                  ctypes.byref(n)))
+    return int(h.value), int(n.value)
+
+
 def cvo_eval_gradient_static(x, fx, z, fz, params: cvo_params, P, ell: float, out,
                              stream=None) -> None:
     """Allocation-free gradient pass on device tensors (torch CUDA float32, or
@@ -510,6 +578,14 @@ class Context:
 
     def serve_stats(self) -> dict:
         return cvo_serve_get_stats(self.ctx)
+
+    def frontend_select(self, depth, hsv, params, out_xyz, out_feat=None, out_pixel=None,
+                        stream=None) -> int:
+        return cvo_frontend_select(self.ctx, depth, hsv, params, out_xyz, out_feat, out_pixel,
+                                   stream)
+
+    def frontend_cloud(self, depth, hsv, params, stream=None):
+        return cvo_frontend_cloud(self.ctx, depth, hsv, params, stream)
 
     @property
     def stream(self) -> int:

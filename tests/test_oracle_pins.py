@@ -400,3 +400,61 @@ def test_trajectory_ground_truth_composes():
     xk = np.linalg.inv(tr["T_wc"][0]) @ w
     xk1 = np.linalg.inv(tr["T_wc"][1]) @ w
     assert np.allclose(tr["P_gt"][0] @ xk1, xk, atol=1e-12)
+
+
+# ---- semi-dense front end (oracle/frontend.py) -----------------------------
+
+def test_frontend_percentile_is_numpys_linear_method():
+    from oracle import frontend
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 100, 1001):
+        v = rng.random(n).astype(np.float32)
+        for q in (0.0, 12.5, 50.0, 80.0, 99.9, 100.0):
+            assert frontend.percentile_linear(v, q) == np.percentile(v.astype(np.float64), q)
+
+
+def test_frontend_gradient_matches_numpy_and_a_pixel_loop():
+    from oracle import frontend
+    rng = np.random.default_rng(4)
+    img = rng.random((9, 13)).astype(np.float32)
+    gx, gy = frontend.gradient_fp32(img)
+    ngy, ngx = np.gradient(img.astype(np.float64))
+    assert np.allclose(gx, ngx, atol=1e-6) and np.allclose(gy, ngy, atol=1e-6)
+    # pixel loop, FP32 arithmetic
+    for y in range(9):
+        for x in range(13):
+            if 0 < x < 12:
+                ref = np.float32(0.5) * (img[y, x + 1] - img[y, x - 1])
+            elif x == 0:
+                ref = img[y, 1] - img[y, 0]
+            else:
+                ref = img[y, 12] - img[y, 11]
+            assert gx[y, x] == ref
+
+
+def test_frontend_selection_on_a_hand_built_image():
+    # a step edge in V between columns 3 and 4 of an 8 x 8 image: the
+    # gradient is nonzero only on columns 3 and 4; with half the pixels
+    # invalid (depth 0) and the 60th percentile, exactly the edge pixels of
+    # the valid rows survive, in raster order, back-projected by the pinhole
+    from oracle import frontend
+    H, W = 8, 8
+    hsv = np.zeros((H, W, 3), np.float32)
+    hsv[:, 4:, 2] = 1.0
+    hsv[..., 0] = 0.25
+    depth = np.full((H, W), 2.0, np.float32)
+    depth[1::2, :] = 0.0
+    xyz, feats, idx = frontend.select(depth, hsv, fx=4.0, fy=4.0, cx=3.5, cy=3.5,
+                                      percentile=60.0)
+    rows = np.arange(0, H, 2)
+    want = np.sort(np.concatenate([rows * W + 3, rows * W + 4]))
+    assert np.array_equal(idx, want)
+    assert np.allclose(xyz[:, 2], 2.0)
+    assert np.allclose(xyz[:, 0], (idx % W - 3.5) / 4.0 * 2.0)
+    assert np.allclose(feats[:, 3], 1.0)          # 0.5 / 0.05 clipped to 1
+    assert np.allclose(feats[:, 0], 0.25)
+    # subsampling takes evenly spaced ranks
+    _, _, idx2 = frontend.select(depth, hsv, fx=4.0, fy=4.0, cx=3.5, cy=3.5, percentile=60.0,
+                                 max_points=3)
+    m = want.size
+    assert np.array_equal(idx2, want[(np.arange(3) * m) // 3])
