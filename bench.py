@@ -223,6 +223,9 @@ def run_cvo(args, world, rank, local):
     D = FX.shape[1]
     ctx = cvo.Context(device=local)
     ht, hs = ctx.set_cloud(X, FX), ctx.set_cloud(Z, FZ)
+    # cell / cluster sizes and work-split costs picked by the library's
+    # autotuner on this pair before anything is timed
+    tune = ctx.autotune(ht, hs)
     stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")
 
@@ -309,7 +312,9 @@ def run_cvo(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points_per_frame": N_POINTS, "feat_dim": D,
                    "l2": "flushed between steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "autotuned": {k: tune[k] for k in ("cell_factor", "cluster_factor",
+                                                      "cost_chunk", "cost_cluster")}},
         "frame_pairs_per_s": world * args.steps / (total_ms * 1e-3),
         "iters_per_solve": statistics.median(iters),
         "pair_evals_per_solve": pairs / (world * args.steps),

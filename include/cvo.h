@@ -329,6 +329,39 @@ int cvo_serve_stop(cvo_ctx* ctx);
  * (zeros if it never ran). */
 int cvo_serve_get_stats(cvo_ctx* ctx, cvo_serve_stats* out);
 
+/* ---- autotuner of the performance parameters ------------------------------ */
+
+typedef struct {
+    int n_cell, n_cluster, n_chunk, n_cluster_cost;  /* candidates per dimension (0: built-in set) */
+    double cell_factor[8];
+    double cluster_factor[8];
+    int cost_chunk[8];
+    int cost_cluster[8];
+    int reps;               /* timed solves per candidate (the fastest counts); 3 */
+} cvo_tune_space;
+
+typedef struct {
+    double start_ms;        /* solve time with the parameters the context had */
+    double best_ms;         /* solve time with the chosen parameters */
+    int candidates;         /* settings timed */
+    double cell_factor, cluster_factor;   /* the chosen setting (also left in the context) */
+    int cost_chunk, cost_cluster;
+} cvo_tune_report;
+
+/* Pick the cell size, the source cluster size and the work-split costs for
+ * the context by timing whole solves of (target, source) from the identity on
+ * the device (CUDA events on the context stream): coordinate descent over
+ * cell_factor, cluster_factor, cost_chunk and cost_cluster, one dimension at a
+ * time, keeping the fastest. Results do not depend on these parameters (the
+ * cutoff test is exact); only the speed does. The context keeps the chosen
+ * values; its cached plans, cell lists and clusters of the two clouds are
+ * dropped and rebuilt on next use. space may be NULL (built-in candidates).
+ * Errors: CVO_ERR_NOT_FOUND, CVO_ERR_BUSY (the request loop runs, or a batch
+ * uses one of the clouds), CVO_ERR_INVALID_ARG (a candidate outside the
+ * parameter ranges of cvo_params). */
+int cvo_autotune(cvo_ctx* ctx, int32_t target, int32_t source, const cvo_tune_space* space,
+                 cvo_tune_report* report);
+
 /* ---- semi-dense front end (Sec. 5: high intensity-gradient pixels) -------- */
 
 typedef struct {

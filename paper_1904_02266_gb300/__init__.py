@@ -41,7 +41,7 @@ EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
            "cvo_batch_create", "cvo_batch_run", "cvo_batch_get_info", "cvo_batch_destroy",
            "cvo_serve_params_default", "cvo_serve_start", "cvo_submit", "cvo_poll",
            "cvo_serve_stop", "cvo_serve_get_stats", "cvo_frontend_params_default",
-           "cvo_frontend_select", "cvo_frontend_cloud",
+           "cvo_frontend_select", "cvo_frontend_cloud", "cvo_autotune",
            "cvo_eval_gradient_static", "cvo_strerror", "cvo_last_error")
 
 
@@ -121,6 +121,20 @@ class cvo_serve_stats(ctypes.Structure):
                 ("idle_exits", ctypes.c_int64)]
 
 
+class cvo_tune_space(ctypes.Structure):
+    _fields_ = [("n_cell", ctypes.c_int), ("n_cluster", ctypes.c_int), ("n_chunk", ctypes.c_int),
+                ("n_cluster_cost", ctypes.c_int), ("cell_factor", ctypes.c_double * 8),
+                ("cluster_factor", ctypes.c_double * 8), ("cost_chunk", ctypes.c_int * 8),
+                ("cost_cluster", ctypes.c_int * 8), ("reps", ctypes.c_int)]
+
+
+class cvo_tune_report(ctypes.Structure):
+    _fields_ = [("start_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("cell_factor", ctypes.c_double),
+                ("cluster_factor", ctypes.c_double), ("cost_chunk", ctypes.c_int),
+                ("cost_cluster", ctypes.c_int)]
+
+
 class cvo_frontend_params(ctypes.Structure):
     _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
                 ("cy", ctypes.c_double), ("depth_min", ctypes.c_double),
@@ -190,6 +204,9 @@ def load_library(path: str = LIB_PATH):
         lib.cvo_frontend_cloud.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, fpp,
                                            ctypes.c_uint32, vp, i32p,
                                            ctypes.POINTER(ctypes.c_int64)]
+        lib.cvo_autotune.argtypes = [vp, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(cvo_tune_space),
+                                     ctypes.POINTER(cvo_tune_report)]
         lib.cvo_stream.argtypes = [vp]
         lib.cvo_stream.restype = ctypes.c_void_p
         lib.cvo_strerror.argtypes = [ctypes.c_int]
@@ -200,7 +217,7 @@ def load_library(path: str = LIB_PATH):
                      "cvo_eval", "cvo_align", "cvo_batch_create", "cvo_batch_run",
                      "cvo_batch_get_info", "cvo_batch_destroy", "cvo_serve_start",
                      "cvo_submit", "cvo_poll", "cvo_serve_stop", "cvo_serve_get_stats",
-                     "cvo_frontend_select", "cvo_frontend_cloud"):
+                     "cvo_frontend_select", "cvo_frontend_cloud", "cvo_autotune"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -467,6 +484,16 @@ def cvo_frontend_cloud(ctx, depth, hsv, params: cvo_frontend_params, stream=None
     return int(h.value), int(n.value)
 
 
+def cvo_autotune(ctx, target: int, source: int, space: cvo_tune_space | None = None) -> dict:
+    """Time solves over the built-in (or given) candidates; the context keeps
+    the fastest setting. Returns the report as a dict."""
+    rep = cvo_tune_report()
+    _check(ctx, load_library().cvo_autotune(ctx, int(target), int(source),
+                                            ctypes.byref(space) if space is not None else None,
+                                            ctypes.byref(rep)))
+    return {k: getattr(rep, k) for k, _ in cvo_tune_report._fields_}
+
+
 def cvo_eval_gradient_static(x, fx, z, fz, params: cvo_params, P, ell: float, out,
                              stream=None) -> None:
     """Allocation-free gradient pass on device tensors (torch CUDA float32, or
@@ -583,6 +610,12 @@ class Context:
                         stream=None) -> int:
         return cvo_frontend_select(self.ctx, depth, hsv, params, out_xyz, out_feat, out_pixel,
                                    stream)
+
+    def autotune(self, target: int, source: int, space=None) -> dict:
+        rep = cvo_autotune(self.ctx, target, source, space)
+        for k in ("cell_factor", "cluster_factor", "cost_chunk", "cost_cluster"):
+            setattr(self.params, k, rep[k])
+        return rep
 
     def frontend_cloud(self, depth, hsv, params, stream=None):
         return cvo_frontend_cloud(self.ctx, depth, hsv, params, stream)

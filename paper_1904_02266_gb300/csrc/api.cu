@@ -1105,3 +1105,175 @@ int cvo_batch_destroy(cvo_ctx* ctx, cvo_batch* b) {
 }
 
 }  // extern "C"
+
+namespace cvo {
+
+namespace {
+
+// Cached structures of a cloud that the tuning changes: its cell lists and
+// clusters, and every plan that uses it.
+void drop_cloud_caches(cvo_ctx* ctx, int32_t h) {
+  for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+    if (it->first.first == h || it->first.second == h) {
+      free_plan(ctx, it->second);
+      it = ctx->plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  if (ctx->eval_plan) {
+    free_plan(ctx, ctx->eval_plan);
+    ctx->eval_plan = nullptr;
+  }
+  Cloud* c = get_cloud(ctx, h);
+  if (!c) return;
+  for (Grid& g : c->grids) {
+    dev_free(ctx, g.xyz);
+    dev_free(ctx, g.feat);
+    dev_free(ctx, g.cell_start);
+    release_bytes(ctx, g.bytes);
+  }
+  c->grids.clear();
+  for (Clusters& k : c->clusters) {
+    dev_free(ctx, k.cstart);
+    release_bytes(ctx, k.bytes);
+  }
+  c->clusters.clear();
+}
+
+// Device time of the fastest of reps solves with parameters prm (after one
+// untimed solve that builds the plan and its cell lists).
+int time_solves(cvo_ctx* ctx, int32_t t, int32_t s, const cvo_params& prm, int reps, double* ms) {
+  ctx->prm = prm;
+  drop_cloud_caches(ctx, t);
+  drop_cloud_caches(ctx, s);
+  Plan* p = nullptr;
+  int rc = build_plan(ctx, t, s, &p);
+  if (rc != CVO_OK) return rc;
+  const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double best = 1e300;
+  rc = run_solve(ctx, p, I, false);
+  if (rc == CVO_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(ctx, CVO_ERR_CUDA, "cudaEventCreate failed");
+  for (int r = 0; r < reps && rc == CVO_OK; ++r) {
+    SolveState* hs = ctx->h_state;
+    std::memset(hs, 0, sizeof(SolveState));
+    std::memcpy(hs->P0, I, sizeof(I));
+    cudaError_t e = cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_solve(p->dp, p->color_mode, p->nblocks, p->d_cfg, p->d_state, p->d_partials,
+                       nullptr, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float f = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+    if (e != cudaSuccess) rc = fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e));
+    best = std::min(best, (double)f);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  free_plan(ctx, p);
+  *ms = best;
+  return rc;
+}
+
+}  // namespace
+
+}  // namespace cvo
+
+extern "C" {
+
+int cvo_autotune(cvo_ctx* ctx, int32_t target, int32_t source, const cvo_tune_space* space,
+                 cvo_tune_report* report) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Cloud* t = get_cloud(ctx, target);
+  Cloud* s = get_cloud(ctx, source);
+  if (!t || !s) return fail(ctx, CVO_ERR_NOT_FOUND, "unknown cloud handle");
+  if (serve_active(ctx))
+    return fail(ctx, CVO_ERR_BUSY, "the request loop is running (cvo_serve_stop ends it)");
+  if (t->refs > 0 || s->refs > 0) return fail(ctx, CVO_ERR_BUSY, "a batch uses the clouds");
+  CK(cudaSetDevice(ctx->device));
+  cvo_tune_space sp{};
+  if (space) sp = *space;
+  const double cells[] = {0.5, 0.6, 0.7, 0.85, 1.0, 1.25};
+  const double clus[] = {1.0, 1.5, 2.0, 2.5, 3.0};
+  const int chunks[] = {8, 16, 24, 32, 48};
+  const int ccl[] = {0, 32, 64, 128};
+  if (sp.n_cell <= 0) {
+    sp.n_cell = 6;
+    std::copy(cells, cells + 6, sp.cell_factor);
+  }
+  if (sp.n_cluster <= 0) {
+    sp.n_cluster = 5;
+    std::copy(clus, clus + 5, sp.cluster_factor);
+  }
+  if (sp.n_chunk <= 0) {
+    sp.n_chunk = 5;
+    std::copy(chunks, chunks + 5, sp.cost_chunk);
+  }
+  if (sp.n_cluster_cost <= 0) {
+    sp.n_cluster_cost = 4;
+    std::copy(ccl, ccl + 4, sp.cost_cluster);
+  }
+  if (sp.reps <= 0) sp.reps = 3;
+  if (sp.n_cell > 8 || sp.n_cluster > 8 || sp.n_chunk > 8 || sp.n_cluster_cost > 8 || sp.reps > 100)
+    return fail(ctx, CVO_ERR_INVALID_ARG, "at most 8 candidates per dimension, 100 repetitions");
+  for (int i = 0; i < sp.n_cell; ++i)
+    if (!(sp.cell_factor[i] >= 0.5 && sp.cell_factor[i] <= 8.0))
+      return fail(ctx, CVO_ERR_INVALID_ARG, "cell_factor candidate outside [0.5, 8]");
+  for (int i = 0; i < sp.n_cluster; ++i)
+    if (!(sp.cluster_factor[i] > 0.0 && sp.cluster_factor[i] <= 8.0))
+      return fail(ctx, CVO_ERR_INVALID_ARG, "cluster_factor candidate outside (0, 8]");
+  for (int i = 0; i < sp.n_chunk; ++i)
+    if (sp.cost_chunk[i] < 0 || sp.cost_chunk[i] > 4096)
+      return fail(ctx, CVO_ERR_INVALID_ARG, "cost_chunk candidate outside [0, 4096]");
+  for (int i = 0; i < sp.n_cluster_cost; ++i)
+    if (sp.cost_cluster[i] < 0 || sp.cost_cluster[i] > 65536)
+      return fail(ctx, CVO_ERR_INVALID_ARG, "cost_cluster candidate outside [0, 65536]");
+  const cvo_params start = ctx->prm;
+  cvo_params best = start;
+  double best_ms = 0.0, start_ms = 0.0;
+  int tried = 0;
+  int rc = time_solves(ctx, target, source, start, sp.reps, &start_ms);
+  best_ms = start_ms;
+  ++tried;
+  for (int dim = 0; dim < 4 && rc == CVO_OK; ++dim) {
+    const int n = dim == 0 ? sp.n_cell : dim == 1 ? sp.n_cluster : dim == 2 ? sp.n_chunk
+                                                                           : sp.n_cluster_cost;
+    cvo_params base = best;
+    for (int i = 0; i < n && rc == CVO_OK; ++i) {
+      cvo_params c = base;
+      if (dim == 0) c.cell_factor = sp.cell_factor[i];
+      else if (dim == 1) c.cluster_factor = sp.cluster_factor[i];
+      else if (dim == 2) c.cost_chunk = sp.cost_chunk[i];
+      else c.cost_cluster = sp.cost_cluster[i];
+      double ms = 0.0;
+      rc = time_solves(ctx, target, source, c, sp.reps, &ms);
+      ++tried;
+      if (rc == CVO_OK && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  ctx->prm = rc == CVO_OK ? best : start;
+  drop_cloud_caches(ctx, target);
+  drop_cloud_caches(ctx, source);
+  if (rc != CVO_OK) return rc;
+  if (report) {
+    report->start_ms = start_ms;
+    report->best_ms = best_ms;
+    report->candidates = tried;
+    report->cell_factor = best.cell_factor;
+    report->cluster_factor = best.cluster_factor;
+    report->cost_chunk = best.cost_chunk;
+    report->cost_cluster = best.cost_cluster;
+  }
+  return CVO_OK;
+}
+
+}  // extern "C"

@@ -67,7 +67,8 @@ def test_struct_layouts_match_the_header(lib_path):
     import paper_1904_02266_gb300 as cvo
     structs = [cvo.cvo_params, cvo.cvo_eval_result, cvo.cvo_stats, cvo.cvo_iter_profile,
                cvo.cvo_batch_info, cvo.cvo_request, cvo.cvo_result, cvo.cvo_serve_params,
-               cvo.cvo_serve_stats, cvo.cvo_frontend_params]
+               cvo.cvo_serve_stats, cvo.cvo_frontend_params, cvo.cvo_tune_space,
+               cvo.cvo_tune_report]
     lines = []
     for st in structs:
         name = st.__name__
