@@ -653,13 +653,22 @@ def order_study():
     print(json.dumps({"order_study": out}), flush=True)
 
 
+def kernel_source_digest() -> str:
+    """First 16 hex digits of the SHA-256 of the solve and queue kernels'
+    source (pair_kernels.cuh, then the dispatcher pair_kernels.cu)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pair_kernels.cuh", "pair_kernels.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1904_02266_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
     summary was taken on the current kernel source (else None)."""
     import glob
     import hashlib
-    src = os.path.join(ROOT, "paper_1904_02266_gb300", "csrc", "pair_kernels.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = kernel_source_digest()
     for path in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_*.md")):
         fields = {}
         for line in open(path):
