@@ -143,82 +143,86 @@ struct BlockCtx {
   float om[3], vc[3];     // unit step direction (centred frame)
   float A, rc2, rplan_f, inv_l2f;
   int w_c0[kWarps], w_j0[kWarps], w_c1[kWarps], w_j1[kWarps];   // warp ranges
+  double dR[9], V[9];     // tail scratch: exp map rotation and its V matrix
 };
 
-__device__ __forceinline__ void cross3d(const double a[3], const double b[3], double o[3]) {
-  o[0] = a[1] * b[2] - a[2] * b[1];
-  o[1] = a[2] * b[0] - a[0] * b[2];
-  o[2] = a[0] * b[1] - a[1] * b[0];
-}
+// ---- the FP64 tail, one warp wide -----------------------------------------
+// On GB300 a warp's FP64 instruction holds the FP64 pipe about as long as a
+// full warp's (about 64 cycles) whatever the number of active lanes, so the
+// tail costs what its count of FP64 instructions costs. It runs on warp 0 of
+// every block with independent components on separate lanes (the 3 x 4 pose
+// product is three instructions, not thirty-six); scalar steps run on every
+// lane at the cost of one. Lanes exchange values by shuffles, or through the
+// block context (shared memory) between __syncwarp()s.
 
-// Centred pose in FP64: R and T' = R cZ + T - cX.
-__device__ void centred_pose(const TailConst& tc, const double P[16], double R[9], double T[3]) {
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    double tr = P[4 * r + 3] - tc.cX[r];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      R[3 * r + c] = P[4 * r + c];
-      tr = fma(P[4 * r + c], tc.cZ[c], tr);
-    }
-    T[r] = tr;
-  }
+__device__ __forceinline__ double flip_sign(double v, bool neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^
+                              (neg ? (long long)0x8000000000000000ull : 0ll));
 }
 
 // Iteration k's constants (ic = the host table's entry k), the FP32 pose, and
-// whether the traversal plan must be rebuilt.
-__device__ void begin_iteration(const IterConst& ic, BlockCtx& b) {
-  b.ell = ic.ell;
-  b.inv_l2 = ic.inv_l2;
-  b.A = ic.A;
-  b.rc2 = ic.rc2;
-  b.inv_l2f = (float)ic.inv_l2;
-  double R[9], T[3];
-  centred_pose(b.tc, b.P, R, T);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) b.R[i] = (float)R[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) b.T[i] = (float)T[i];
+// whether the traversal plan must be rebuilt. Warp 0, every lane.
+__device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
+  // centred pose [R T'] on lanes 0..11, element (r, c) = (l / 4, l % 4):
+  // R = the pose's rotation, T' = R cZ + T - cX
+  const int l = min(lane, 11), r = l >> 2, c = l & 3;
+  const double t3 = fma(b.P[4 * r + 2], b.tc.cZ[2],
+                        fma(b.P[4 * r + 1], b.tc.cZ[1],
+                            fma(b.P[4 * r], b.tc.cZ[0], b.P[4 * r + 3] - b.tc.cX[r])));
+  const double v = c == 3 ? t3 : b.P[4 * r + c];
   // is the current plan still a superset of the pairs within the cutoff?
   const double need = (double)ic.rprune;   // 1.001 r_c
   // reuse only at an unchanged lengthscale (the floor of the schedule): while
   // ell shrinks a fresh, tighter plan costs less than the extra candidates
   bool replan = b.need_plan || ic.level != b.plan_level || ic.ell != b.plan_ell;
   if (!replan) {
-    double d2r[9], d2t[3];
+    const double d = v - (c == 3 ? b.Tp[r] : b.Rp[3 * r + c]);
+    const double sq = lane < 12 ? d * d : 0.0;
+    double sr = c < 3 ? sq : 0.0, st = c == 3 ? sq : 0.0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d2r[i] = (R[i] - b.Rp[i]) * (R[i] - b.Rp[i]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d2t[i] = (T[i] - b.Tp[i]) * (T[i] - b.Tp[i]);
-    // pairwise sums: short dependent chains (FP64 latency dominates the tail)
-    const double dr = ((d2r[0] + d2r[1]) + (d2r[2] + d2r[3])) +
-                      ((d2r[4] + d2r[5]) + (d2r[6] + d2r[7])) + d2r[8];
-    const double dt = (d2t[0] + d2t[1]) + d2t[2];
+    for (int off = 8; off > 0; off >>= 1) {
+      sr += __shfl_xor_sync(kFull, sr, off);
+      st += __shfl_xor_sync(kFull, st, off);
+    }
+    sr = __shfl_sync(kFull, sr, 0);
+    st = __shfl_sync(kFull, st, 0);
     // |dR z + dT| <= |dR|_F |z| + |dT| for every source point, |z| <= r_src
-    const double drift = ((double)sqrtf((float)dr) * b.tc.src_radius + (double)sqrtf((float)dt)) *
+    const double drift = ((double)sqrtf((float)sr) * b.tc.src_radius + (double)sqrtf((float)st)) *
                              (1.0 + 1e-5) + 1e-6 * need;
     replan = (need + drift > b.r_plan) || (b.r_plan > kLoose * (need + drift));
   }
-  b.level = ic.level;
-  if (replan) {
-    b.need_plan = 1;
-    b.plan_level = ic.level;
-    b.plan_ell = ic.ell;
-    b.r_plan = need * (1.0 + kSkin);
-    b.rplan_f = (float)b.r_plan;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) b.Rp[i] = R[i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) b.Tp[i] = T[i];
+  __syncwarp();   // every lane has read the old plan pose
+  if (lane < 12) {
+    if (c < 3) b.R[3 * r + c] = (float)v;
+    else b.T[r] = (float)v;
+    if (replan) {
+      if (c < 3) b.Rp[3 * r + c] = v;
+      else b.Tp[r] = v;
+    }
   }
+  if (lane == 0) {
+    b.ell = ic.ell;
+    b.inv_l2 = ic.inv_l2;
+    b.A = ic.A;
+    b.rc2 = ic.rc2;
+    b.inv_l2f = (float)ic.inv_l2;
+    b.level = ic.level;
+    if (replan) {
+      b.need_plan = 1;
+      b.plan_level = ic.level;
+      b.plan_ell = ic.ell;
+      b.r_plan = need * (1.0 + kSkin);
+      b.rplan_f = (float)b.r_plan;
+    }
+  }
+  __syncwarp();
 }
 
-// FP64 reciprocal from the FP32 one and two Newton steps r <- r (2 - x r)
-// (each squares the relative error: 1e-7 -> 1e-14 -> 1e-28). Finite,
-// nonzero x within FP32 range.
+// FP64 reciprocal from the FP32 one and a Newton step r <- r (2 - x r) (which
+// squares the relative error: 1e-7 -> 1e-14). Finite, nonzero x within FP32
+// range.
 __device__ __forceinline__ double recip_refined(double x) {
   double r = (double)(1.0f / (float)x);
-  r = r * fma(-x, r, 2.0);
   r = r * fma(-x, r, 2.0);
   return r;
 }
@@ -229,8 +233,8 @@ __device__ __forceinline__ double recip_refined(double x) {
 // pattern of G' decides: for c3 < 0 the + -> - crossings are r1 and r3, for
 // c3 > 0 only r2; with one real root r, only c3 < 0 gives a crossing.
 // The decisions (which case, which root) are taken on FP64 quantities; the
-// chosen root is evaluated in FP32 and then polished by two FP64 Newton steps
-// on the cubic itself, so the result has FP64 accuracy without FP64
+// chosen root is evaluated in FP32 and then polished by an FP64 Newton step on
+// the cubic itself (relative error about 1e-14), without FP64
 // transcendentals. The coefficients are first scaled by a power of two
 // (exact) so that the largest has magnitude in [0.5, 1).
 __device__ bool first_maximiser(double c0, double c1, double c2, double c3, double* t_out) {
@@ -297,9 +301,9 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
       t = -1.0;   // triple root: G'' vanishes there, so it is not a strict maximum
     }
   }
-  if (t > 0.0) {  // two Newton polishes on the cubic, slope inverted in FP32
+  if (t > 0.0) {  // a Newton polish on the cubic, slope inverted in FP32
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < 1; ++it) {
       const double f = fma(fma(fma(c3, t, c2), t, c1), t, c0);
       const double fp = fma(fma(3.0 * c3, t, 2.0 * c2), t, c1);
       const float fpf = (float)fp;
@@ -316,152 +320,166 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
   return false;
 }
 
-// exp of the twist tw = t (omega, v) in SE(3), Eq. step. The coefficients
-// sin(th)/th, (1 - cos th)/th^2 and (th - sin th)/th^3 are even functions of
-// th; below th = 0.5 they are summed as Taylor series in th^2 (truncation
-// error < 1e-16), above it from sin and cos.
-__device__ void exp_se3(const double tw[6], double dR[9], double dT[3]) {
-  const double* phi = tw;
-  const double* rho = tw + 3;
-  const double x = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
-  double A, B, C;
-  if (x < 0.25) {
-    A = 1.0 + x * (-1.0 / 6 + x * (1.0 / 120 + x * (-1.0 / 5040 + x * (1.0 / 362880 +
-        x * (-1.0 / 39916800 + x * (1.0 / 6227020800.0))))));
-    B = 0.5 + x * (-1.0 / 24 + x * (1.0 / 720 + x * (-1.0 / 40320 + x * (1.0 / 3628800 +
-        x * (-1.0 / 479001600 + x * (1.0 / 87178291200.0))))));
-    C = 1.0 / 6 + x * (-1.0 / 120 + x * (1.0 / 5040 + x * (-1.0 / 362880 + x * (1.0 / 39916800 +
-        x * (-1.0 / 6227020800.0 + x * (1.0 / 1307674368000.0))))));
-  } else {
-    const double th = sqrt(x);
-    const double s = sin(th), hs = sin(0.5 * th);
-    A = s / th;
-    B = 2.0 * hs * hs / x;
-    C = (th - s) / (x * th);
-  }
-  const double W[9] = {0.0, -phi[2], phi[1], phi[2], 0.0, -phi[0], -phi[1], phi[0], 0.0};
-  double W2[9];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      W2[3 * i + j] = W[3 * i] * W[j] + W[3 * i + 1] * W[3 + j] + W[3 * i + 2] * W[6 + j];
-  double V[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const double I = (i % 4 == 0) ? 1.0 : 0.0;
-    dR[i] = I + A * W[i] + B * W2[i];
-    V[i] = I + B * W[i] + C * W2[i];
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    dT[i] = V[3 * i] * rho[0] + V[3 * i + 1] * rho[1] + V[3 * i + 2] * rho[2];
-}
+// Exp-map series (Eq. step): sin(th)/th, (1 - cos th)/th^2 and (th - sin th)/th^3
+// as polynomials in x = th^2 (truncation error < 1e-16 for x < 0.25), one per
+// lane 0..2.
+__constant__ double kExpSeries[3][7] = {
+    {1.0, -1.0 / 6, 1.0 / 120, -1.0 / 5040, 1.0 / 362880, -1.0 / 39916800, 1.0 / 6227020800.0},
+    {0.5, -1.0 / 24, 1.0 / 720, -1.0 / 40320, 1.0 / 3628800, -1.0 / 479001600,
+     1.0 / 87178291200.0},
+    {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800, -1.0 / 6227020800.0,
+     1.0 / 1307674368000.0}};
 
 // Gradient tail: sums (F, omega', v, pairs, candidates) -> F, metric
-// gradient, unit step direction in the centred frame.
-__device__ void finish_gradient(BlockCtx& b, const double sums[9]) {
-  const double s2 = b.tc.sigma2;
-  const double v[3] = {sums[4], sums[5], sums[6]};
-  double cxv[3];
-  cross3d(b.tc.cX, v, cxv);
-  const double ka = s2 * b.inv_l2 * b.tc.inv_a2, kb = s2 * b.inv_l2 * b.tc.inv_b2;
-  double nrm2 = 0.0;
+// gradient (lanes 0..5), unit step direction in the centred frame. Warp 0.
+__device__ void finish_gradient(BlockCtx& b, const double* sums, int lane) {
+  const TailConst& tc = b.tc;
+  const double kf = tc.sigma2 * b.inv_l2;
+  // component a of xi on lane a < 6: (omega'_a + (cX x v)_a) k_a or v_a k_b
+  const int a = lane % 3, a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
+  const bool rot = lane < 3;
+  const double cr = fma(tc.cX[a1], sums[4 + a2], -(tc.cX[a2] * sums[4 + a1]));
+  const double x0 = sums[1 + min(lane, 5)] + (rot ? cr : 0.0);
+  const double x = lane < 6 ? x0 * (kf * (rot ? tc.inv_a2 : tc.inv_b2)) : 0.0;
+  double nrm2 = x * x;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    b.xi[a] = (sums[1 + a] + cxv[a]) * ka;
-    b.xi[3 + a] = v[a] * kb;
-  }
-#pragma unroll
-  for (int a = 0; a < 6; ++a) nrm2 += b.xi[a] * b.xi[a];
-  // |xi| and 1/|xi|: FP32 rsqrt refined by two FP64 Newton steps
-  // y <- y (1.5 - 0.5 x y^2) (relative error 1e-7 -> 1e-14 -> 1e-28)
+  for (int off = 4; off > 0; off >>= 1) nrm2 += __shfl_xor_sync(kFull, nrm2, off);
+  nrm2 = __shfl_sync(kFull, nrm2, 0);
+  // |xi| and 1/|xi|: FP32 rsqrt refined by an FP64 Newton step
+  // y <- y (1.5 - 0.5 x y^2) (relative error 1e-7 -> 1e-14)
   double inv = 0.0, nrm = 0.0;
-  if (nrm2 > 0.0 && nrm2 < 1e300) {
-    inv = (double)rsqrtf((float)nrm2);
-    if (inv > 0.0 && isfinite(inv)) {
-      inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
-      inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
-      nrm = nrm2 * inv;
-    } else {
-      nrm = sqrt(nrm2);
-      inv = 1.0 / nrm;
-    }
+  const float r32 = nrm2 > 0.0 && nrm2 < 1e30 ? rsqrtf((float)nrm2) : 0.0f;
+  if (r32 > 0.0f && isfinite(r32)) {
+    inv = (double)r32;
+    inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
+    nrm = nrm2 * inv;
   } else if (nrm2 > 0.0) {
     nrm = sqrt(nrm2);
     inv = 1.0 / nrm;
   }
-  b.xi_norm = nrm;
-  b.F = s2 * sums[0];
-  b.nnz_grad = (unsigned long long)sums[7];
-  b.cand_grad = (unsigned long long)sums[8];
-  double wxc[3];
-  cross3d(b.xi, b.tc.cX, wxc);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    b.om[a] = (float)(b.xi[a] * inv);
-    b.vc[a] = (float)((b.xi[3 + a] + wxc[a]) * inv);
+  // unit direction: omega_a = xi_a / |xi|, v'_a = (v_a + (omega x cX)_a) / |xi|
+  const double xa1 = __shfl_sync(kFull, x, a1), xa2 = __shfl_sync(kFull, x, a2);
+  const double xv = __shfl_sync(kFull, x, 3 + a);
+  const double vc = (xv + fma(xa1, tc.cX[a2], -(xa2 * tc.cX[a1]))) * inv;
+  const double om = x * inv;
+  if (lane < 6) b.xi[lane] = x;
+  if (lane < 3) {
+    b.om[a] = (float)om;
+    b.vc[a] = (float)vc;
   }
+  if (lane == 0) {
+    b.xi_norm = nrm;
+    b.F = tc.sigma2 * sums[0];
+    b.nnz_grad = (unsigned long long)sums[7];
+    b.cand_grad = (unsigned long long)sums[8];
+  }
+  __syncwarp();
 }
 
-// Step tail: S0..S4, step length, pose update, stop test.
-__device__ void finish_step(BlockCtx& b, const double sums[7]) {
+// Step tail: S0..S4, step length, pose update P <- exp(t xi) P, stop test.
+// Warp 0.
+__device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
   const TailConst& tc = b.tc;
   const double nxi = b.xi_norm;
-  double pw = tc.sigma2;
-#pragma unroll
-  for (int m = 0; m < 5; ++m) {  // the sums were taken along xi / |xi|
-    b.S[m] = sums[m] * pw;
-    pw *= nxi;
+  // S_m = sums_m sigma^2 |xi|^m on lane m < 5 (the sums were taken along xi / |xi|)
+  const int m = min(lane, 4);
+  const double n2 = nxi * nxi;
+  double pw = (m & 1) ? nxi : 1.0;
+  if (m & 2) pw *= n2;
+  if (m & 4) pw *= n2 * n2;
+  const double Sm = sums[m] * (tc.sigma2 * pw);
+  const double S1 = __shfl_sync(kFull, Sm, 1), S2 = __shfl_sync(kFull, Sm, 2);
+  const double S3 = __shfl_sync(kFull, Sm, 3), S4 = __shfl_sync(kFull, Sm, 4);
+  if (lane < 5) b.S[lane] = Sm;
+  if (lane == 0) {
+    b.nnz_total += b.nnz_grad + (unsigned long long)sums[5];
+    b.cand_total += b.cand_grad + (unsigned long long)sums[6];
   }
-  b.nnz_total += b.nnz_grad + (unsigned long long)sums[5];
-  b.cand_total += b.cand_grad + (unsigned long long)sums[6];
   if (tc.mode == kModeEval) {
-    b.done = 1;
+    if (lane == 0) b.done = 1;
+    __syncwarp();
     return;
   }
+  // the step length (the same scalar work on every lane)
   double t;
-  if (!(nxi > 0.0) || !(b.S[1] > 0.0)) {
+  int no_ascent = 0, fallback = 0;
+  if (!(nxi > 0.0) || !(S1 > 0.0)) {
     t = 0.0;
-    b.no_ascent += 1;
+    no_ascent = 1;
   } else {
     bool ok;
     if (tc.step_order == 2) {
-      ok = b.S[2] < 0.0;
-      t = ok ? -b.S[1] / (2.0 * b.S[2]) : 0.0;
+      ok = S2 < 0.0;
+      t = ok ? -S1 / (2.0 * S2) : 0.0;
     } else {
-      ok = first_maximiser(b.S[1], 2.0 * b.S[2], 3.0 * b.S[3], 4.0 * b.S[4], &t);
+      ok = first_maximiser(S1, 2.0 * S2, 3.0 * S3, 4.0 * S4, &t);
     }
     if (!ok) {
-      b.fallback += 1;
+      fallback = 1;
       t = b.have_t_prev ? 0.5 * b.t_prev : 1e-3 / nxi;
     }
   }
-  // P <- exp(t xi) P
-  double tw[6], dR[9], dT[3];
+  // twist t xi: rotation phi (lanes 0..2), translation rho (lanes 3..5)
+  const double tw = t * b.xi[min(lane, 5)];
+  const double p0 = __shfl_sync(kFull, tw, 0), p1 = __shfl_sync(kFull, tw, 1);
+  const double p2 = __shfl_sync(kFull, tw, 2);
+  const double r0 = __shfl_sync(kFull, tw, 3), r1 = __shfl_sync(kFull, tw, 4);
+  const double r2 = __shfl_sync(kFull, tw, 5);
+  const double x = fma(p0, p0, fma(p1, p1, p2 * p2));
+  // A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3 on lanes 0, 1, 2
+  double coef;
+  if (x < 0.25) {
+    const double* k = kExpSeries[min(lane, 2)];
+    coef = k[6];
 #pragma unroll
-  for (int a = 0; a < 6; ++a) tw[a] = t * b.xi[a];
-  exp_se3(tw, dR, dT);
-  double Pn[12];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-      Pn[4 * r + c] = dR[3 * r] * b.P[c] + dR[3 * r + 1] * b.P[4 + c] + dR[3 * r + 2] * b.P[8 + c];
-    Pn[4 * r + 3] += dT[r];
+    for (int i = 5; i >= 0; --i) coef = fma(coef, x, k[i]);
+  } else {
+    const double th = sqrt(x);
+    const double sn = sin(th), hs = sin(0.5 * th);
+    coef = lane == 0 ? sn / th : lane == 1 ? 2.0 * hs * hs / x : (th - sn) / (x * th);
   }
-#pragma unroll
-  for (int i = 0; i < 12; ++i) b.P[i] = Pn[i];
-  b.t = t;
-  b.t_prev = t;
-  b.have_t_prev = 1;
-  const bool conv = (b.ell == tc.ell_floor) &&
-                    (fabs(t) * nxi < tc.eps_pose || nxi < tc.eps_grad);
-  b.k += 1;
-  if (conv || b.k >= tc.max_iters) {
-    b.done = 1;
-    b.converged = conv ? 1 : 0;
+  const double A = __shfl_sync(kFull, coef, 0), B = __shfl_sync(kFull, coef, 1);
+  const double C = __shfl_sync(kFull, coef, 2);
+  // M = I + c1 W + c2 W^2 (W = hat(phi), W^2 = phi phi^T - |phi|^2 I): lanes 0..8
+  // give dR = I + A W + B W^2, lanes 9..17 V = I + B W + C W^2 (Eq. step)
+  const int q = lane % 9, i = q / 3, j = q % 3;
+  const double pi = i == 0 ? p0 : i == 1 ? p1 : p2;
+  const double pj = j == 0 ? p0 : j == 1 ? p1 : p2;
+  const int kk = 3 - i - j;   // the third index when i != j
+  const double pk = kk == 0 ? p0 : kk == 1 ? p1 : p2;
+  const double w = i == j ? 0.0 : flip_sign(pk, (j - i + 3) % 3 == 1);
+  const double w2 = fma(pi, pj, i == j ? -x : 0.0);
+  const bool first = lane < 9;
+  const double mv = fma(first ? A : B, w, fma(first ? B : C, w2, i == j ? 1.0 : 0.0));
+  if (lane < 9) b.dR[q] = mv;
+  else if (lane < 18) b.V[q] = mv;
+  __syncwarp();
+  // dT = V rho on lanes 0..2
+  const int rr = lane % 3;
+  const double dt = fma(b.V[3 * rr], r0, fma(b.V[3 * rr + 1], r1, b.V[3 * rr + 2] * r2));
+  // P <- [dR dT] P on lanes 0..11, element (r, c) = (l / 4, l % 4)
+  const int l = min(lane, 11), r = l >> 2, c = l & 3;
+  const double dtr = __shfl_sync(kFull, dt, r);
+  const double pn = fma(b.dR[3 * r], b.P[c],
+                        fma(b.dR[3 * r + 1], b.P[4 + c],
+                            fma(b.dR[3 * r + 2], b.P[8 + c], c == 3 ? dtr : 0.0)));
+  __syncwarp();   // every lane has read the old pose
+  if (lane < 12) b.P[lane] = pn;
+  if (lane == 0) {
+    b.no_ascent += no_ascent;
+    b.fallback += fallback;
+    b.t = t;
+    b.t_prev = t;
+    b.have_t_prev = 1;
+    const bool conv = (b.ell == tc.ell_floor) &&
+                      (fabs(t) * nxi < tc.eps_pose || nxi < tc.eps_grad);
+    b.k += 1;
+    if (conv || b.k >= tc.max_iters) {
+      b.done = 1;
+      b.converged = conv ? 1 : 0;
+    }
   }
+  __syncwarp();
 }
 
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
@@ -513,53 +531,35 @@ __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) 
   return *s_flag != 0;
 }
 
-// Fixed-order FP64 sum of the nblk (<= 2 * kThreads) block partials: thread t
-// loads blocks t and t + kThreads of every value at once (one L2 round trip),
-// then a shuffle tree per warp and the warps in order. Results land in out[]
-// (shared). Must be called by every thread of the block.
+// Fixed-order FP64 sum of the nblk (<= 2 * kThreads) block partials. Thread t
+// takes value i = t % 16 of the blocks t / 16, t / 16 + 16, ... (loads
+// coalesced across the 16 values of a block; FP64 adds in sequence, every lane
+// busy, so few FP64 instructions), then the two halves of each warp and the
+// eight warps in order. Results land in out[] (shared). Must be called by
+// every thread of the block.
 template <class Smem>
 __device__ void reduce_partials(const double* partials, int nvals, double* out, int nblk,
                                 Smem& sm) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const bool f32 = sm.b.tc.reduce_fp32 != 0;
-  double v[kPartialStride];
-#pragma unroll
-  for (int i = 0; i < kPartialStride; ++i) {
-    double a = 0.0, c = 0.0;
-    if (i < nvals) {
-      if (t < nblk) a = __ldcg(&partials[(size_t)t * kPartialStride + i]);
-      if (t + kThreads < nblk) c = __ldcg(&partials[(size_t)(t + kThreads) * kPartialStride + i]);
-    }
-    v[i] = a + c;
-  }
-  // value sums (all but the two trailing counts) in FP32 when asked to
-#pragma unroll
-  for (int i = 0; i < kPartialStride; ++i) {
-    if (i < nvals) {
-      double w;
-      if (f32 && i < nvals - 2) {
-        float x = (float)v[i];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(kFull, x, off);
-        w = (double)x;
-      } else {
-        w = warp_sum_d(v[i]);
-      }
-      if (lane == 0) sm.red_d[warp][i] = w;
+  const int i = t & 15, b0 = t >> 4;
+  const bool f32 = sm.b.tc.reduce_fp32 != 0 && i < nvals - 2;   // counts stay exact
+  double acc = 0.0;
+  float accf = 0.f;
+  if (i < nvals) {
+    for (int blk = b0; blk < nblk; blk += kThreads / 16) {
+      const double v = __ldcg(&partials[(size_t)blk * kPartialStride + i]);
+      if (f32) accf += (float)v;
+      else acc += v;
     }
   }
+  if (f32) acc = (double)accf;
+  acc += __shfl_xor_sync(kFull, acc, 16);
+  if (lane < 16 && i < nvals) sm.red_d[warp][i] = acc;
   __syncthreads();
   if (t < nvals) {
     double r = 0.0;
-    if (f32 && t < nvals - 2) {
-      float rf = 0.f;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) rf += (float)sm.red_d[w][t];
-      r = (double)rf;
-    } else {
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) r += sm.red_d[w][t];
-    }
+    for (int w = 0; w < kWarps; ++w) r += sm.red_d[w][t];
     out[t] = r;
   }
   __syncthreads();
@@ -745,7 +745,7 @@ struct SolveSmem {
   int xs[kWarps][kMaxSeg];
   int pf[kWarps][kMaxSeg + 1];
   float red[kWarps][10];
-  double red_d[kWarps][kPartialStride];
+  double red_d[kWarps][16];
   long long scan[kThreads];
   long long bnd_base[2 * kWarps];   // work offset of the group holding each warp boundary
   int bnd_group[2 * kWarps];
@@ -1287,15 +1287,12 @@ __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* pa
   if (warp == 0 && lane < NACC + 2) {
     double s = 0.0;
     if (lane < NACC) {
-      if (sm.b.tc.reduce_fp32) {   // precision study: the sums stay FP32 to the end
-        float f = 0.f;
+      // the block's eight warp sums in FP32 (fixed order); FP64 starts with the
+      // cross-block reduction
+      float f = 0.f;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) f += sm.red[w][lane];
-        s = (double)f;
-      } else {
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += (double)sm.red[w][lane];
-      }
+      for (int w = 0; w < kWarps; ++w) f += sm.red[w][lane];
+      s = (double)f;
     } else {
       unsigned long long n = 0;
 #pragma unroll
@@ -1372,8 +1369,9 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     for (int i = 0; i < 5; ++i) b.S[i] = 0.0;
     b.r_plan = 0.0;
     b.plan_ell = 0.0;
-    if (!b.done) begin_iteration(cfg->iters[0], b);
   }
+  __syncthreads();
+  if (warp == 0 && !sm.b.done) begin_iteration(cfg->iters[0], sm.b, lane);
   __syncthreads();
   if (join && !team_join(st, team.size, sm)) {
     if (tid == 0) sm.b.done = 1;   // a team that never assembled runs no iteration
@@ -1423,9 +1421,9 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     if (stamp) tg1 = globaltimer();
     if (!grid_sync_reduce(st, gen, sm, part_g, 9, team.size)) break;
     if (stamp) tg2 = globaltimer();
-    if (tid == 0) {
-      sm.b.collect_kept = 0;
-      finish_gradient(sm.b, sm.sums);
+    if (warp == 0) {
+      if (lane == 0) sm.b.collect_kept = 0;
+      finish_gradient(sm.b, sm.sums, lane);
     }
     __syncthreads();
     if (stamp) t2 = globaltimer();
@@ -1434,31 +1432,30 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     if (stamp) ts1 = globaltimer();
     if (!grid_sync_reduce(st, gen, sm, part_s, 7, team.size)) break;
     if (stamp) ts2 = globaltimer();
-    {
-      if (tid == 0) {
-        BlockCtx& b = sm.b;
-        const int k = b.k;
-        // the next iteration's constants, loaded now and used after the tail
-        const IterConst ic_next = cfg->iters[min(k + 1, b.tc.max_iters - 1)];
-        const unsigned long long pairs_before = b.nnz_total;
-        finish_step(b, sm.sums);
-        if (stamp && k < b.tc.max_iters) {
-          IterRecord& r = records[k];
-          r.ell = b.ell;
-          r.t_plan_ns = (float)(t1 - t0);
-          r.t_grad_ns = (float)(t2 - t1);
-          r.t_step_ns = (float)(globaltimer() - t2);
-          r.t_grad_pass_ns = (float)(tg1 - t1);
-          r.t_grad_sync_ns = (float)(tg2 - t1);
-          r.t_step_pass_ns = (float)(ts1 - t2);
-          r.t_step_sync_ns = (float)(ts2 - t2);
-          r.replanned = replan;
-          r.grad_pairs = (long long)b.nnz_grad;
-          r.step_pairs = (long long)(b.nnz_total - pairs_before - b.nnz_grad);
-          r.grad_candidates = (long long)b.cand_grad;
-        }
-        if (!b.done) begin_iteration(ic_next, b);
+    if (warp == 0) {
+      BlockCtx& b = sm.b;
+      const int k = b.k;
+      // the next iteration's constants, loaded now and used after the tail
+      const IterConst ic_next = cfg->iters[min(k + 1, b.tc.max_iters - 1)];
+      const unsigned long long pairs_before = b.nnz_total;
+      finish_step(b, sm.sums, lane);
+      if (stamp && k < b.tc.max_iters) {
+        IterRecord& r = records[k];
+        r.ell = b.ell;
+        r.t_plan_ns = (float)(t1 - t0);
+        r.t_grad_ns = (float)(t2 - t1);
+        r.t_step_ns = (float)(globaltimer() - t2);
+        r.t_grad_pass_ns = (float)(tg1 - t1);
+        r.t_grad_sync_ns = (float)(tg2 - t1);
+        r.t_step_pass_ns = (float)(ts1 - t2);
+        r.t_step_sync_ns = (float)(ts2 - t2);
+        r.replanned = replan;
+        r.grad_pairs = (long long)b.nnz_grad;
+        r.step_pairs = (long long)(b.nnz_total - pairs_before - b.nnz_grad);
+        r.grad_candidates = (long long)b.cand_grad;
       }
+      __syncwarp();
+      if (!b.done) begin_iteration(ic_next, b, lane);
     }
     __syncthreads();
   }
