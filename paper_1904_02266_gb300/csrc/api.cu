@@ -200,7 +200,8 @@ int ensure_clusters(cvo_ctx* ctx, Cloud* c, const std::vector<float>& max_edges,
                     std::vector<int>* index_out) {
   index_out->assign(max_edges.size(), -1);
   std::vector<size_t> built;   // indices into c->clusters built by this call
-  cudaError_t e = cudaSuccess;
+  std::vector<float> edges;
+  std::vector<int*> starts, counts;
   for (size_t l = 0; l < max_edges.size(); ++l) {
     for (size_t i = 0; i < c->clusters.size(); ++i)
       if (c->clusters[i].max_edge == max_edges[l]) (*index_out)[l] = (int)i;
@@ -210,18 +211,22 @@ int ensure_clusters(cvo_ctx* ctx, Cloud* c, const std::vector<float>& max_edges,
     k.max_edge = max_edges[l];
     int rc = dev_alloc(ctx, (void**)&k.cstart, sizeof(int) * (c->n + 2), &k.bytes);
     if (rc != CVO_OK) return rc;
-    int* d_ncl = k.cstart + c->n + 1;
-    e = build_clusters(c->zs, (int)c->n, c->mf, k.max_edge, k.cstart, d_ncl, ctx->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ctx->h_int + built.size(), d_ncl, sizeof(int), cudaMemcpyDeviceToHost,
-                          ctx->stream);
     k.ncl = -1;   // filled after the synchronisation
+    edges.push_back(k.max_edge);
+    starts.push_back(k.cstart);
+    counts.push_back(k.cstart + c->n + 1);
     c->clusters.push_back(k);
     built.push_back(c->clusters.size() - 1);
     (*index_out)[l] = (int)c->clusters.size() - 1;
-    if (e != cudaSuccess) break;
   }
-  if (e == cudaSuccess && !built.empty()) e = cudaStreamSynchronize(ctx->stream);
+  if (built.empty()) return CVO_OK;
+  // every missing level in one launch, their counts read with one synchronisation
+  cudaError_t e = build_clusters(c->zs, (int)c->n, c->mf, edges.data(), starts.data(),
+                                 counts.data(), (int)built.size(), ctx->stream);
+  for (size_t j = 0; j < built.size() && e == cudaSuccess; ++j)
+    e = cudaMemcpyAsync(ctx->h_int + j, counts[j], sizeof(int), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     for (size_t j = built.size(); j-- > 0;) {
       Clusters& k = c->clusters[built[j]];

@@ -196,11 +196,12 @@ cudaError_t morton_order(const float4* xyz, const void* feat, int n, int dp, int
                          bool bf16, const MortonFrame& mf, float4* out_xyz, void* out_feat,
                          cudaMemPool_t pool, cudaStream_t s);
 
-// Cut a Morton-ordered cloud into clusters: runs sharing the Morton prefix of
-// an octree node with edge <= max_edge, split into runs of <= kClusterMax.
-// cstart receives ncl + 1 offsets (capacity n + 1); *d_ncl the count.
-cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, float max_edge,
-                           int* cstart, int* d_ncl, cudaStream_t s);
+// Cut a Morton-ordered cloud into clusters, for nlev (<= kMaxLevels) cluster
+// sizes in one launch: for level l, runs sharing the Morton prefix of an
+// octree node with edge <= max_edge[l], split into runs of <= kClusterMax;
+// cstart[l] receives ncl + 1 offsets (capacity n + 1), *d_ncl[l] the count.
+cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, const float* max_edge,
+                           int* const* cstart, int* const* d_ncl, int nlev, cudaStream_t s);
 
 // Build a cell list of edge h over a packed cloud.
 cudaError_t build_grid(const float4* xyz, const void* feat, int n, int dp, int n_pad, bool bf16,

@@ -261,9 +261,19 @@ __global__ void morton_keys_kernel(const float4* __restrict__ xyz, int n, float 
 // One block of 1024 threads walks the Morton-ordered cloud in tiles. A
 // cluster starts where the node prefix changes (a new octree node) or every
 // kClusterMax points inside one node; tile carries keep the scan exact.
+// One block per requested level (octree depth): block l cuts the Morton-
+// ordered points into the clusters of level l.
+struct ClusterLevels {
+  int shift[kMaxLevels];
+  int* cstart[kMaxLevels];
+  int* ncl_out[kMaxLevels];
+};
+
 __global__ void build_clusters_kernel(const float4* __restrict__ xyz, int n, float lox,
-                                      float loy, float loz, float scale, int shift,
-                                      int* __restrict__ cstart, int* __restrict__ ncl_out) {
+                                      float loy, float loz, float scale, ClusterLevels lv) {
+  const int shift = lv.shift[blockIdx.x];
+  int* __restrict__ cstart = lv.cstart[blockIdx.x];
+  int* __restrict__ ncl_out = lv.ncl_out[blockIdx.x];
   __shared__ int s_a[1024];
   __shared__ int s_b[1024];
   const int tid = threadIdx.x;
@@ -467,18 +477,24 @@ cudaError_t morton_order(const float4* xyz, const void* feat, int n, int dp, int
   return e;
 }
 
-cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, float max_edge,
-                           int* cstart, int* d_ncl, cudaStream_t s) {
-  // deepest octree level whose node edge still fits max_edge
-  int L = 0;
-  float edge = mf.cell * (float)(1 << kMortonBits);
-  while (L < kMortonBits && edge > max_edge) {
-    edge *= 0.5f;
-    ++L;
+cudaError_t build_clusters(const float4* xyz, int n, const MortonFrame& mf, const float* max_edge,
+                           int* const* cstart, int* const* d_ncl, int nlev, cudaStream_t s) {
+  if (nlev <= 0) return cudaSuccess;
+  if (nlev > kMaxLevels) return cudaErrorInvalidValue;
+  ClusterLevels lv{};
+  for (int l = 0; l < nlev; ++l) {
+    // deepest octree level whose node edge still fits max_edge[l]
+    int L = 0;
+    float edge = mf.cell * (float)(1 << kMortonBits);
+    while (L < kMortonBits && edge > max_edge[l]) {
+      edge *= 0.5f;
+      ++L;
+    }
+    lv.shift[l] = 3 * (kMortonBits - L);
+    lv.cstart[l] = cstart[l];
+    lv.ncl_out[l] = d_ncl[l];
   }
-  const int shift = 3 * (kMortonBits - L);
-  build_clusters_kernel<<<1, 1024, 0, s>>>(xyz, n, mf.lo[0], mf.lo[1], mf.lo[2], mf.scale, shift,
-                                           cstart, d_ncl);
+  build_clusters_kernel<<<nlev, 1024, 0, s>>>(xyz, n, mf.lo[0], mf.lo[1], mf.lo[2], mf.scale, lv);
   return cudaGetLastError();
 }
 
