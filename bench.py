@@ -57,18 +57,22 @@ WORKLOAD = ("room VGA pair: 640x480 ray-cast room (6x5x3 m box + 20 cuboids), "
             "80th-percentile gradient pixels subsampled to 20000 points/frame, 3 deg / 3 cm "
             "motion, 5-D features, ell 0.15 x0.9 -> 0.02, kcut 1e-3, <= 200 iterations")
 
-# FP32 roofline of the pair passes (GB300: 152 SMs x 128 FP32 lanes, FMA = 2 flops,
-# 2070 MHz maximum SM clock) and the FP32 flops each kept pair needs.
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-PEAK_FP32_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# FP32/MUFU roofline of the pair passes. Peaks from the unit counts and the
+# maximum SM clock: 152 SMs x 128 FP32 lanes (one FP32 instruction per lane
+# per clock) and 16 MUFU (ex2) lanes per SM, at 2070 MHz.
+SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 16, 2070.0
+PEAK_FP32_TINST = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12   # 40.3 T FP32 instructions/s
+PEAK_MUFU_TINST = SMS * MUFU_LANES * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def flops_per_pair(D: int) -> dict:
-    """Algorithmic FP32 flops per kept pair (FMA = 2). Gradient pass:
-    e (3) + |e|^2 (5) + feature difference and norm (3D - 1) + exponent (2) +
-    accumulation of w and w e (7). Step pass: e, |e|^2, features, exponent as
-    above, beta (5), gamma/delta/eps (18), g2..g4 (16), accumulation of S0..S4 (9)."""
-    return {"grad": 16 + 3 * D, "step": 57 + 3 * D}
+def work_per_pair(D: int) -> dict:
+    """Algorithmic work per kept pair, in FP32 instructions (plus one MUFU ex2):
+    gradient pass 22 (e 3, |e|^2 3, feature differences D, their squares D,
+    exponent 2, accumulation of w and w e 4, at D = 5); step pass 52 (the
+    gradient pass's 18 before its accumulation, beta..eps, g^1..g^4 and the
+    five accumulations). Rejected candidates and per-chunk / per-cluster work
+    are overhead, not algorithmic."""
+    return {"grad": 12 + 2 * D, "step": 42 + 2 * D, "mufu": 1}
 
 
 def parse_args():
@@ -82,6 +86,10 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--tuned", default="",
+                    help="cell_factor=..,cluster_factor=..,cost_chunk=..,cost_cluster=..: use "
+                         "these instead of running the autotuner (to profile the setting a "
+                         "plain run chose)")
     ap.add_argument("--odometry", action="store_true",
                     help="instead of the benchmark line, print odometry over a rendered trajectory")
     ap.add_argument("--order-study", action="store_true",
@@ -221,11 +229,21 @@ def run_cvo(args, world, rank, local):
     d = synth.room_pair(N_POINTS, seed=synth.seed_for(2))
     X, FX, Z, FZ = d["X"], d["FX"], d["Z"], d["FZ"]
     D = FX.shape[1]
-    ctx = cvo.Context(device=local)
+    fixed = {}
+    for kv in filter(None, args.tuned.split(",")):
+        k, v = kv.split("=")
+        if k not in ("cell_factor", "cluster_factor", "cost_chunk", "cost_cluster"):
+            raise SystemExit(f"--tuned: unknown parameter {k}")
+        fixed[k] = int(v) if k.startswith("cost") else float(v)
+    ctx = cvo.Context(device=local, **fixed)
     ht, hs = ctx.set_cloud(X, FX), ctx.set_cloud(Z, FZ)
     # cell / cluster sizes and work-split costs picked by the library's
-    # autotuner on this pair before anything is timed
-    tune = ctx.autotune(ht, hs)
+    # autotuner on this pair before anything is timed (or given by --tuned)
+    if fixed:
+        tune = {k: getattr(ctx.params, k) for k in ("cell_factor", "cluster_factor", "cost_chunk",
+                                                     "cost_cluster")}
+    else:
+        tune = ctx.autotune(ht, hs)
     stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")
 
@@ -276,15 +294,19 @@ def run_cvo(args, world, rank, local):
     d2h = 16 * 8 + ctypes.sizeof(cvo.cvo_stats)
 
     # roofline of the solve kernel (the only kernel of a timed step): algorithmic
-    # FP32 flops of the kept pairs of one solve over the CUDA-event time per
-    # solve; the per-phase split comes from the kernel's own timestamps
+    # FP32 instructions of the kept pairs of one solve over the CUDA-event time
+    # per solve; the per-phase split comes from the kernel's own timestamps
     _, pst, recs = ctx.align_profile(ht, hs)
-    fpp = flops_per_pair(D)
+    wpp = work_per_pair(D)
     grad_pairs = sum(r["grad_pairs"] for r in recs)
     step_pairs = sum(r["step_pairs"] for r in recs)
     cand = sum(r["grad_candidates"] for r in recs)
-    flops_per_solve = grad_pairs * fpp["grad"] + step_pairs * fpp["step"]
-    achieved = flops_per_solve / (ms / args.steps * 1e-3) / 1e12
+    inst_per_solve = grad_pairs * wpp["grad"] + step_pairs * wpp["step"]
+    solve_s = ms / args.steps * 1e-3
+    achieved = inst_per_solve / solve_s / 1e12
+    # roofline time: the larger of the FP32 and MUFU times of the kept pairs
+    t_roof = max(inst_per_solve / (PEAK_FP32_TINST * 1e12),
+                 (grad_pairs + step_pairs) * wpp["mufu"] / (PEAK_MUFU_TINST * 1e12))
     phases = {k: sum(r[k] for r in recs) for k in ("plan_ms", "grad_ms", "step_ms")}
     traffic = recorded_traffic("solve_kernel")
 
@@ -313,6 +335,7 @@ def run_cvo(args, world, rank, local):
         "config": {"workload": WORKLOAD, "points_per_frame": N_POINTS, "feat_dim": D,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single",
+                   "tuning": "fixed by --tuned" if fixed else "autotuned before timing",
                    "autotuned": {k: tune[k] for k in ("cell_factor", "cluster_factor",
                                                       "cost_chunk", "cost_cluster")}},
         "frame_pairs_per_s": world * args.steps / (total_ms * 1e-3),
@@ -325,10 +348,15 @@ def run_cvo(args, world, rank, local):
                 "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "solve_kernel", "achieved": achieved,
-                     "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
-                     "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                     "flops_per_launch": flops_per_solve,
+                     "peak": PEAK_FP32_TINST, "unit": "T FP32 inst/s",
+                     "frac": achieved / PEAK_FP32_TINST, "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)",
+                     "work": f"{wpp['grad']} FP32 inst per kept gradient-pass pair, "
+                             f"{wpp['step']} per kept step-pass pair, 1 MUFU ex2 each",
+                     "inst_per_launch": inst_per_solve,
+                     "roofline_ms": t_roof * 1e3,
+                     "frac_at_sampled_clock": (t_roof / solve_s) * SM_MAX_MHZ
+                                              / max(1.0, (clocks or {}).get("sm_mhz") or SM_MAX_MHZ),
                      "phase_ms_per_solve": phases},
         "clocks": clocks,
     }
@@ -393,7 +421,13 @@ def bench_batch(cvo, torch, local, n_pairs, flush):
     return {"workload": f"{n_pairs} uneven planes pairs, 2k-40k points, motions <= 5 deg / 5 cm, "
                         f"ell0 ~ U[0.12, 0.18]",
             "ms_per_batch": t_batch, "frame_pairs_per_s": n_pairs / (t_batch * 1e-3),
-            "gpairs_per_s": pe / (t_batch * 1e-3) / 1e9, "blocks": info["blocks"],
+            "gpairs_per_s": pe / (t_batch * 1e-3) / 1e9,
+            # both passes of an iteration keep the same pairs, so a pair evaluation
+            # costs (grad + step) / 2 algorithmic FP32 instructions on average
+            "roofline_frac": pe / (t_batch * 1e-3) * 0.5 * (work_per_pair(5)["grad"]
+                                                             + work_per_pair(5)["step"])
+                             / (PEAK_FP32_TINST * 1e12),
+            "blocks": info["blocks"],
             "max_team": info["max_team"], "graph": info["graph"],
             "plain": {"ms": plain_ms, "frame_pairs_per_s": n_pairs / (plain_ms * 1e-3),
                       "gpairs_per_s": plain_pe / (plain_ms * 1e-3) / 1e9},

@@ -95,8 +95,8 @@ typedef struct {
     /* performance tuning (results do not depend on these): */
     double cluster_factor; /* source cluster (octree node) edge as a multiple of the cell edge,
                               capped so a cluster spans at most 8 x 8 cell rows; 2.0 */
-    int cost_chunk;        /* work split: per-chunk overhead in pair-test units; 24 */
-    int cost_cluster;      /* work split: cost of staging one cluster in pair-test units; 64 */
+    int cost_chunk;        /* work split: per-chunk overhead in pair-test units; 48 */
+    int cost_cluster;      /* work split: cost of staging one cluster in pair-test units; 32 */
     double cost_kept;      /* work split of a reused plan: cost of a kept pair in pair-test
                               units, from the kept pairs counted by the plan's first gradient
                               pass (the split is redone once, at the plan's second iteration);

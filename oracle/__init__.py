@@ -293,9 +293,11 @@ def align(X, FX, Z, FZ, P0, prm: Params, record: bool = False) -> dict:
     either |t xi| < eps_pose or |xi| < eps_grad (Table 1), or after max_iters.
     When the quartic has no maximiser on t > 0, the step is half the previous
     one (1e-3/|xi| on the first iteration) and the iteration is counted in
-    ``fallback_steps``. When S1 <= 0 (S1 is the metric norm of xi, so this
+    ``fallback_steps``. When |xi| < eps_grad (below the gradient threshold of
+    Table 1's stop test) or S1 <= 0 (S1 is the metric norm of xi, so this
     happens only when xi is at rounding level) no step is taken and the
-    iteration is counted in ``no_ascent_steps``.
+    iteration is counted in ``no_ascent_steps``: a xi at rounding level can
+    still give S1 > 0, and the quartic's root along it is then arbitrary.
     """
     P = _c(P0).reshape(4, 4).copy()
     ells = ell_schedule(prm, prm.max_iters)
@@ -314,7 +316,7 @@ def align(X, FX, Z, FZ, P0, prm: Params, record: bool = False) -> dict:
         nxi = float(np.linalg.norm(xi))
         s2 = pair_sums(X, FX, Z, FZ, P, ell, prm, xi=xi)
         nnz_total += s["nnz"] + s2["nnz"]
-        if nxi == 0.0 or not s2["S"][1] > 0.0:
+        if nxi == 0.0 or nxi < prm.eps_grad or not s2["S"][1] > 0.0:
             t = 0.0
             no_ascent += 1
         else:

@@ -101,6 +101,9 @@ void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
   dev_free(ctx, p->seg_pref);
   dev_free(ctx, p->cl_nseg);
   dev_free(ctx, p->cl_cand);
+  dev_free(ctx, p->seg_fpref);
+  dev_free(ctx, p->cl_fcand);
+  dev_free(ctx, p->cl_box);
   dev_free(ctx, p->cl_kept);
   dev_free(ctx, p->group_agg);
   release_bytes(ctx, p->bytes);
@@ -110,6 +113,8 @@ void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
   p->d_partials = nullptr;
   p->d_records = nullptr;
   p->seg_xs = p->seg_pref = p->cl_nseg = p->cl_cand = p->cl_kept = nullptr;
+  p->seg_fpref = p->cl_fcand = nullptr;
+  p->cl_box = nullptr;
   p->group_agg = nullptr;
   p->bytes = 0;
   p->cap_iters = p->cap_ncl = 0;
@@ -282,6 +287,9 @@ int reserve_plan(cvo_ctx* ctx, Plan* p, int iters, int ncl, int nblocks) {
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->seg_pref, sizeof(int) * (size_t)ncl * kMaxSeg, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_nseg, sizeof(int) * ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_cand, sizeof(int) * ncl, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->seg_fpref, sizeof(int) * (size_t)ncl * kMaxSeg, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_fcand, sizeof(int) * ncl, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_box, sizeof(float4) * 2 * (size_t)ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_kept, sizeof(int) * ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->group_agg, sizeof(long long) * ng, &p->bytes);
   if (rc != CVO_OK) {
@@ -363,6 +371,9 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   cfg.seg_pref = p->seg_pref;
   cfg.cl_nseg = p->cl_nseg;
   cfg.cl_cand = p->cl_cand;
+  cfg.seg_fpref = p->seg_fpref;
+  cfg.cl_fcand = p->cl_fcand;
+  cfg.cl_box = p->cl_box;
   cfg.cl_kept = p->cl_kept;
   cfg.group_agg = p->group_agg;
   cfg.src_radius = s->radius;
@@ -573,8 +584,8 @@ void cvo_params_default(cvo_params* p) {
   p->feat_dim = 5;
   p->cell_factor = 0.7;
   p->cluster_factor = 2.0;
-  p->cost_chunk = 24;
-  p->cost_cluster = 64;
+  p->cost_chunk = 48;
+  p->cost_cluster = 32;
   p->cost_kept = 0.0;
   p->team_factor = 6.0;
 }
@@ -1206,7 +1217,7 @@ int cvo_autotune(cvo_ctx* ctx, int32_t target, int32_t source, const cvo_tune_sp
   if (space) sp = *space;
   const double cells[] = {0.5, 0.6, 0.7, 0.85, 1.0, 1.25};
   const double clus[] = {1.0, 1.5, 2.0, 2.5, 3.0};
-  const int chunks[] = {8, 16, 24, 32, 48};
+  const int chunks[] = {16, 32, 48, 64, 96};
   const int ccl[] = {0, 32, 64, 128};
   if (sp.n_cell <= 0) {
     sp.n_cell = 6;

@@ -79,7 +79,12 @@ struct SolveCfg {
   int* seg_xs;             // first target index of each segment, ncl_max * kMaxSeg
   int* seg_pref;           // candidate offset of each segment in its cluster
   int* cl_nseg;            // segments per cluster
-  int* cl_cand;            // candidates per cluster
+  int* cl_cand;            // candidates per cluster (every point of its segments)
+  int* seg_fpref;          // offset of each segment among the cluster's filtered candidates
+  int* cl_fcand;           // filtered candidates per cluster: those within the plan radius
+                           //   of the cluster's bounding box
+  float4* cl_box;          // per cluster: bounding box of its transformed points at the
+                           //   plan pose (lo, hi)
   int* cl_kept;            // kept pairs per cluster in the first gradient pass of a plan
   long long* group_agg;    // work of each group of 32 consecutive clusters
   double src_radius;       // max |z'| over the centred source (bounds pose drift)
@@ -112,7 +117,8 @@ struct SolveState {
   unsigned long long nnz_total, cand_total;
   unsigned long long nnz_pass[2], cand_pass[2];
   unsigned long long nnz_eval, cand_eval;   // gradient pass of the last iteration
-  unsigned int bar_count, bar_gen;          // grid barrier (zeroed before each launch)
+  unsigned int bar_count, bar_rel;          // grid barrier: arrivals, and the last generation whose
+                                            // totals are published (zeroed before each launch)
   unsigned int join_count, leave_count;     // queued solves: blocks of the team that have started
                                             // and that are done with the entry
   unsigned long long t_begin_ns, t_end_ns;  // global timer at the start and end of the solve

@@ -13,19 +13,23 @@
 // One iteration (every block runs the same sequence; phases are separated by
 // a grid barrier whose spin is bounded):
 //  plan        (only when needed) one warp per source cluster (an octree node
-//              of the source, at most 32 points): transform, bounding box, and
-//              the rows of target cells within the plan radius, stored as
-//              segments of the cell-sorted target.                     barrier
-//              pair-test totals of groups of 32 clusters.               barrier
+//              of the source, at most 32 points): transform, bounding box, the
+//              rows of target cells within the plan radius, stored as segments
+//              of the cell-sorted target, and (clusters with at most
+//              kFilterMax candidates) the count of candidates within the plan
+//              radius of the box, per segment.                         barrier
+//              work totals of groups of 32 clusters.                    barrier
 //              every block scans the group totals and places its own warps on
-//              an even split of the pair tests (no further barrier).
-//  gradient    each warp walks its share of 32-candidate chunks: one lane per
-//  pass        candidate target point (coalesced load into registers, next
-//              chunk prefetched) against the cluster's source points staged in
-//              shared memory (broadcast reads). FP32 pairs, one ex2.approx per
-//              kept pair, per-lane FP32 sums, fixed-order reductions.  barrier
-//  tail        every block reduces all block partials in FP64 in the same
-//              order and runs the same FP64 tail, so no broadcast is needed.
+//              an even split of the work, cut at groups of four source points
+//              (no further barrier).
+//  gradient    each warp walks its share of chunks of 32 filtered candidates:
+//  pass        one lane per candidate target point against the cluster's
+//              source points staged in shared memory (broadcast reads). FP32
+//              pairs, one ex2.approx per kept pair, per-lane FP32 sums,
+//              fixed-order reductions.                                 barrier
+//  tail        the block that completes the barrier reduces all block
+//              partials in FP64 in a fixed order and publishes the totals;
+//              every block runs the same FP64 tail, so no broadcast is needed.
 //  step pass   as above along the unit direction.                      barrier
 //  tail        step length, exponential-map update, next iteration.
 // The plan is reused while it still covers the cutoff: it is built with a
@@ -58,6 +62,7 @@ constexpr unsigned kSpinLimit = 1u << 22;   // barrier polls before giving up (~
 constexpr unsigned long long kJoinLimitNs = 60ull * 1000 * 1000 * 1000;
 constexpr double kSkin = 0.10;              // plan radius margin (fraction of the cutoff)
 constexpr double kLoose = 1.25;             // replan when the plan radius exceeds this factor
+constexpr int kFilterMax = 1024;            // candidates of a cluster the plan filters at most
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -142,7 +147,9 @@ struct BlockCtx {
   float R[9], T[3];       // FP32 centred pose: z~' = R z' + T
   float om[3], vc[3];     // unit step direction (centred frame)
   float A, rc2, rplan_f, inv_l2f;
-  int w_c0[kWarps], w_j0[kWarps], w_c1[kWarps], w_j1[kWarps];   // warp ranges
+  // warp ranges: from group g0 of chunk j0 of cluster c0 up to (not
+  // including) group g1 of chunk j1 of cluster c1
+  int w_c0[kWarps], w_j0[kWarps], w_g0[kWarps], w_c1[kWarps], w_j1[kWarps], w_g1[kWarps];
   double dR[9], V[9];     // tail scratch: exp map rotation and its V matrix
 };
 
@@ -227,16 +234,34 @@ __device__ __forceinline__ double recip_refined(double x) {
   return r;
 }
 
+// FP64 reciprocal and square root of any finite x != 0 (x > 0): the
+// refined FP32 forms inside FP32's range, the FP64 operations outside it.
+__device__ __forceinline__ double rcp64(double x) {
+  const double ax = fabs(x);
+  return (ax > 1e-30 && ax < 1e30) ? recip_refined(x) : 1.0 / x;
+}
+
+__device__ __forceinline__ double sqrt64(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return sqrt(x);
+  // y ~ 1/sqrt(x) from FP32, two FP64 Newton steps y <- y (1.5 - 0.5 x y^2)
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return x * y;
+}
+
 // Smallest positive t at which G'(t) = c0 + c1 t + c2 t^2 + c3 t^3 changes sign
 // from + to - (the first local maximum of the quartic model, Sec. 4 "Step
-// size"), given c0 = S1 > 0. With three real roots r1 < r2 < r3 the sign
-// pattern of G' decides: for c3 < 0 the + -> - crossings are r1 and r3, for
-// c3 > 0 only r2; with one real root r, only c3 < 0 gives a crossing.
-// The decisions (which case, which root) are taken on FP64 quantities; the
-// chosen root is evaluated in FP32 and then polished by an FP64 Newton step on
-// the cubic itself (relative error about 1e-14), without FP64
-// transcendentals. The coefficients are first scaled by a power of two
-// (exact) so that the largest has magnitude in [0.5, 1).
+// size"), given c0 = S1 > 0. The coefficients are first scaled by a power of
+// two (exact) so that the largest has magnitude in [0.5, 1). The critical
+// points of G' (the real roots of G'' = c1 + 2 c2 t + 3 c3 t^2) cut t > 0 into
+// pieces on which G' is monotone; the first piece whose right end has G' < 0
+// (for the last piece, the sign of the leading coefficient) holds the answer,
+// which a Newton iteration kept inside the shrinking bracket finds in FP64.
+// Its start is the root of the closed-form cubic evaluated in FP32 (cbrt /
+// acos / cos, no FP64 transcendentals), or the bracket's midpoint: a close
+// start takes two steps; a far one (the FP32 form loses the small roots of a
+// cubic whose roots differ by orders of magnitude) a few more.
 __device__ bool first_maximiser(double c0, double c1, double c2, double c3, double* t_out) {
   const double s = fmax(fmax(fabs(c0), fabs(c1)), fmax(fabs(c2), fabs(c3)));
   if (!(s > 0.0) || !isfinite(s)) return false;
@@ -254,25 +279,25 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
   c1 *= sc;
   c2 *= sc;
   c3 *= sc;
-  double t = -1.0;
+  if (fabs(c3) < 1e-30) c3 = 0.0;
+  if (fabs(c2) < 1e-30) c2 = 0.0;
+  // start: a root of the cubic from the closed form in FP32 (any root; the
+  // bracket below decides which one is wanted); a negligible cubic term is
+  // left out of the start only
+  double t32 = -1.0;
   if (fabs(c3) <= 1e-12) {
-    // quadratic c2 t^2 + c1 t + c0 (or linear)
     if (fabs(c2) <= 1e-12) {
-      if (c1 < 0.0) t = (double)(-(float)c0 / (float)c1);
+      if (c1 < 0.0) t32 = (double)(-(float)c0 / (float)c1);
     } else {
       const double disc = c1 * c1 - 4.0 * c2 * c0;
       if (disc >= 0.0) {
         const float qf = -0.5f * ((float)c1 + copysignf(sqrtf((float)disc), (float)c1));
         const float ra = qf / (float)c2, rb = (float)c0 / qf;
-        const float lo = fminf(ra, rb), hi = fmaxf(ra, rb);
-        // c2 < 0: + between the roots, so + -> - at the larger root;
-        // c2 > 0: + outside them, so + -> - at the smaller root
-        t = (double)((c2 < 0.0) ? hi : lo);
-        if (!(t > 0.0)) t = -1.0;
+        t32 = (double)((c2 < 0.0) ? fmaxf(ra, rb) : fminf(ra, rb));
       }
     }
   } else {
-    const double r3 = recip_refined(c3);
+    const double r3 = rcp64(c3);
     const double B = c2 * r3, C = c1 * r3, D = c0 * r3;
     const double B3 = B * (1.0 / 3.0);
     const double p = fma(-B, B3, C);
@@ -280,41 +305,135 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
     const double disc = fma(0.25 * q, q, (1.0 / 27.0) * p * p * p);
     const float pf = (float)p, qf = (float)q, B3f = (float)B3;
     if (disc > 0.0) {
-      if (c3 < 0.0) {
-        const float u = -copysignf(cbrtf(0.5f * fabsf(qf) + sqrtf((float)disc)), qf);
-        t = (double)((u != 0.0f ? u - pf / (3.0f * u) : 0.0f) - B3f);
-      }
+      const float u = -copysignf(cbrtf(0.5f * fabsf(qf) + sqrtf((float)disc)), qf);
+      t32 = (double)((u != 0.0f ? u - pf / (3.0f * u) : 0.0f) - B3f);
     } else if (p < 0.0) {
       // roots m cos(phi - 2 pi k / 3) - B/3: k = 0 largest, k = 1 middle, k = 2 smallest
       const float m = 2.0f * sqrtf(-pf * (1.0f / 3.0f));
       const float arg = fminf(1.0f, fmaxf(-1.0f, 3.0f * qf / (pf * m)));
       const float phi = acosf(arg) * (1.0f / 3.0f);
       const float two_pi_3 = 2.09439510239319549f;
-      if (c3 < 0.0) {
-        // (the hardware cosine is accurate enough for a start the polish refines)
-        const float r1 = m * __cosf(phi - 2.0f * two_pi_3) - B3f;
-        t = (double)(r1 > 0.0f ? r1 : m * __cosf(phi) - B3f);
-      } else {
-        t = (double)(m * __cosf(phi - two_pi_3) - B3f);   // k = 1: middle root
+      // the hardware cosine is accurate enough for a start
+      const float rk[3] = {m * __cosf(phi) - B3f, m * __cosf(phi - two_pi_3) - B3f,
+                           m * __cosf(phi - 2.0f * two_pi_3) - B3f};
+      // the smallest positive one that G' crosses from + to - (as far as FP32 tells)
+      t32 = -1.0;
+      for (int k = 0; k < 3; ++k) {
+        const double tk = (double)rk[k];
+        if (tk > 0.0 && fma(fma(3.0 * c3, tk, 2.0 * c2), tk, c1) < 0.0 && (t32 < 0.0 || tk < t32))
+          t32 = tk;
       }
-    } else {
-      t = -1.0;   // triple root: G'' vanishes there, so it is not a strict maximum
     }
   }
-  if (t > 0.0) {  // a Newton polish on the cubic, slope inverted in FP32
-#pragma unroll
-    for (int it = 0; it < 1; ++it) {
+  // fast path: Newton from the closed-form root; accepted when it converges
+  // (a first step below 1e-7 t: the start was FP32-accurate and one step
+  // squares that error) and G'' < 0 on [0, t] (then G' falls from c0 > 0 over
+  // [0, t], so t is its first root and a + -> - crossing)
+  if (isfinite(t32) && t32 > 0.0) {
+    double t = t32;
+    bool conv = false;
+    for (int it = 0; it < 3; ++it) {
       const double f = fma(fma(fma(c3, t, c2), t, c1), t, c0);
       const double fp = fma(fma(3.0 * c3, t, 2.0 * c2), t, c1);
-      const float fpf = (float)fp;
-      if (fpf != 0.0f && isfinite(fpf)) {
-        const double tn = fma(-f, (double)(1.0f / fpf), t);
-        if (tn > 0.0 && isfinite(tn)) t = tn;
-      }
+      if (!(fp < 0.0) || !isfinite(fp)) break;
+      const double tn = fma(-f, rcp64(fp), t);
+      if (!(tn > 0.0) || !isfinite(tn)) break;
+      conv = fabs(tn - t) <= (it == 0 ? 1e-7 : 1e-13) * tn;
+      t = tn;
+      if (conv) break;
+    }
+    // G''(0) = c1 < 0, G''(t) < 0, and for concave G'' (c3 < 0) with its
+    // vertex -c2 / (3 c3) inside (0, t), the vertex value c1 - c2^2 / (3 c3) < 0
+    if (conv && c1 < 0.0 && fma(fma(3.0 * c3, t, 2.0 * c2), t, c1) < 0.0 &&
+        (!(c3 < 0.0 && c2 > 0.0 && c2 < -3.0 * c3 * t) || 3.0 * c1 * c3 > c2 * c2)) {
+      *t_out = t;
+      return true;
     }
   }
+  // positive critical points of G', ascending
+  double e0 = -1.0, e1 = -1.0;
+  if (c3 != 0.0) {
+    const double dd = fma(c2, c2, -3.0 * c1 * c3);   // discriminant of G'' over 4
+    if (dd > 0.0) {
+      const double qq = -(c2 + copysign(sqrt64(dd), c2));   // G'' roots: qq / (3 c3), c1 / qq
+      double ra = qq * rcp64(3.0 * c3);
+      double rb = qq != 0.0 ? c1 * rcp64(qq) : ra;
+      if (ra > rb) {
+        const double tmp = ra;
+        ra = rb;
+        rb = tmp;
+      }
+      if (ra > 0.0) {
+        e0 = ra;
+        if (rb > ra) e1 = rb;
+      } else if (rb > 0.0) {
+        e0 = rb;
+      }
+    }
+  } else if (c2 != 0.0) {
+    const double r = -c1 * rcp64(2.0 * c2);
+    if (r > 0.0) e0 = r;
+  }
+  // the first monotone piece (lo, hi) on which G' falls below zero
+  const double lead = c3 != 0.0 ? c3 : c2 != 0.0 ? c2 : c1;
+  double lo = 0.0, hi = -1.0;   // hi < 0: unbounded
+  bool found = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (found) break;
+    const double b = k == 0 ? e0 : k == 1 ? e1 : -1.0;
+    if (k < 2 && !(b > lo)) continue;   // no such critical point
+    const double fb = b > 0.0 ? fma(fma(fma(c3, b, c2), b, c1), b, c0) : lead;
+    if (fb < 0.0) {
+      hi = b;
+      found = true;
+    } else if (b > 0.0) {
+      lo = b;   // G' >= 0 at the end of this piece: no crossing in it
+    } else {
+      break;    // the last piece stays positive: no maximiser
+    }
+  }
+  if (!found) return false;
+  // Newton on G' inside [lo, hi] (G' > 0 at lo, < 0 at hi), bisection or
+  // doubling when a step leaves the bracket; bounded. Start: the closed-form
+  // root if it lies in the bracket, else the smallest point where a falling
+  // term balances c0, (c0 / |c_k|)^(1/k), else the bracket's middle.
+  const auto inside = [&](double x) { return isfinite(x) && x > lo && (hi < 0.0 || x < hi); };
+  double t = t32;
+  if (!inside(t)) {
+    double tb = -1.0;
+    if (c1 < 0.0) tb = c0 / -c1;
+    if (c2 < 0.0) {
+      const double r = (double)sqrtf((float)(c0 / -c2));
+      if (r > 0.0 && (tb < 0.0 || r < tb)) tb = r;
+    }
+    if (c3 < 0.0) {
+      const double r = (double)cbrtf((float)(c0 / -c3));
+      if (r > 0.0 && (tb < 0.0 || r < tb)) tb = r;
+    }
+    t = inside(tb) ? tb : hi > 0.0 ? 0.5 * (lo + hi) : (lo > 0.0 ? 2.0 * lo : 1.0);
+  }
+  for (int it = 0; it < 64; ++it) {
+    const double f = fma(fma(fma(c3, t, c2), t, c1), t, c0);
+    if (f > 0.0) lo = t;
+    else if (f < 0.0) hi = t;
+    else break;
+    const double fp = fma(fma(3.0 * c3, t, 2.0 * c2), t, c1);
+    double tn = (fp < 0.0 && isfinite(fp)) ? fma(-f, rcp64(fp), t) : -1.0;
+    if (tn > 0.0 && isfinite(tn) && fabs(tn - t) <= 1e-13 * tn) {
+      t = tn;   // converged (the step is below the resolution of t)
+      break;
+    }
+    if (!inside(tn)) {
+      if (hi < 0.0) tn = 2.0 * fmax(t, lo);
+      else if (lo > 0.0 && hi > 4.0 * lo) tn = sqrt64(lo * hi);
+      else if (lo == 0.0) tn = 0.25 * hi;
+      else tn = 0.5 * (lo + hi);
+    }
+    t = tn;
+  }
   if (t > 0.0 && isfinite(t)) {
-    *t_out = t;
+    *t_out = t;   // scaling all coefficients by one factor leaves the roots alone
     return true;
   }
   return false;
@@ -370,8 +489,8 @@ __device__ void finish_gradient(BlockCtx& b, const double* sums, int lane) {
   if (lane == 0) {
     b.xi_norm = nrm;
     b.F = tc.sigma2 * sums[0];
-    b.nnz_grad = (unsigned long long)sums[7];
-    b.cand_grad = (unsigned long long)sums[8];
+    b.nnz_grad = (unsigned long long)__double_as_longlong(sums[7]);
+    b.cand_grad = (unsigned long long)__double_as_longlong(sums[8]);
   }
   __syncwarp();
 }
@@ -392,8 +511,8 @@ __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
   const double S3 = __shfl_sync(kFull, Sm, 3), S4 = __shfl_sync(kFull, Sm, 4);
   if (lane < 5) b.S[lane] = Sm;
   if (lane == 0) {
-    b.nnz_total += b.nnz_grad + (unsigned long long)sums[5];
-    b.cand_total += b.cand_grad + (unsigned long long)sums[6];
+    b.nnz_total += b.nnz_grad + (unsigned long long)__double_as_longlong(sums[5]);
+    b.cand_total += b.cand_grad + (unsigned long long)__double_as_longlong(sums[6]);
   }
   if (tc.mode == kModeEval) {
     if (lane == 0) b.done = 1;
@@ -403,7 +522,9 @@ __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
   // the step length (the same scalar work on every lane)
   double t;
   int no_ascent = 0, fallback = 0;
-  if (!(nxi > 0.0) || !(S1 > 0.0)) {
+  // no step along a gradient below the stop test's threshold (at rounding
+  // level S1 can still be positive, and the quartic's root is then arbitrary)
+  if (!(nxi > 0.0) || nxi < tc.eps_grad || !(S1 > 0.0)) {
     t = 0.0;
     no_ascent = 1;
   } else {
@@ -482,24 +603,22 @@ __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
   __syncwarp();
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// The team barrier counts arrivals on one counter that is never reset during
+// a launch: generation g is complete when (g + 1) * nblk blocks have arrived.
+// Thread 0 of each block adds its arrival (no return value awaited) and polls
+// the counter; no block has to release the others.
+__device__ __forceinline__ void barrier_arrive(SolveState* st) {
+  __threadfence();   // the block's writes before the barrier, at GPU scope
+  atomicAdd(&st->bar_count, 1u);
 }
 
-// Release the barrier of generation g (thread 0 of the last block to arrive).
-__device__ __forceinline__ void barrier_release(SolveState* st, unsigned g) {
-  atomicExch(&st->bar_count, 0u);
-  __threadfence();
-  st_release_u32(&st->bar_gen, g + 1);
-}
-
-// Wait for generation g to be released (thread 0). A block that polls
-// kSpinLimit times raises kStatusTimeout and returns false; its team then
-// leaves the solve loop when the other blocks' own waits run out at the next
-// barrier, which the timed-out block never reaches (an error path, bounded).
-__device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned g) {
+// Wait until `target` arrivals (thread 0). A block that polls kSpinLimit times
+// raises kStatusTimeout and returns false; its team then leaves the solve loop
+// when the other blocks' own waits run out at the next barrier, which the
+// timed-out block never reaches (an error path, bounded).
+__device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned target) {
   unsigned spins = 0;
-  while (ld_acquire(&st->bar_gen) == g) {
+  while (ld_acquire(&st->bar_count) < target) {
     if (++spins > kSpinLimit) {
       atomicOr(&st->status, (int)kStatusTimeout);
       return false;
@@ -515,88 +634,119 @@ __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) 
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned g = gen;
+    barrier_arrive(st);
+    const int ok = barrier_wait(st, (g + 1) * (unsigned)nblk) ? 1 : 0;
     __threadfence();
-    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-    int ok = 1;
-    if (arrived == (unsigned)nblk - 1) {
-      barrier_release(st, g);
-    } else {
-      ok = barrier_wait(st, g) ? 1 : 0;
-    }
-    __threadfence();
-    gen = g + 1;
     *s_flag = ok;
   }
+  gen += 1;
   __syncthreads();
   return *s_flag != 0;
 }
 
-// Fixed-order FP64 sum of the nblk (<= 2 * kThreads) block partials. Thread t
-// takes value i = t % 16 of the blocks t / 16, t / 16 + 16, ... (loads
-// coalesced across the 16 values of a block; FP64 adds in sequence, every lane
-// busy, so few FP64 instructions), then the two halves of each warp and the
-// eight warps in order. Results land in out[] (shared). Must be called by
-// every thread of the block.
+// Fixed-order FP64 sum of the nblk block partials (nvals <= 10 values each;
+// the last two are counts, held as 64-bit integers in the doubles' bits), by
+// one block. Warp w < nvals - 2 sums value w: lane l adds the value of blocks
+// l, l + 32, l + 64, ... in sequence (its loads issued first), then the 32 lane
+// sums are added along a fixed shuffle tree, so every FP64 instruction has all
+// its lanes busy (on GB300 an FP64 instruction costs the same with one lane or
+// 32). Warp 7 adds the two counts as integers. Results land in out[] (shared).
+// Every thread of the block calls it.
 template <class Smem>
 __device__ void reduce_partials(const double* partials, int nvals, double* out, int nblk,
                                 Smem& sm) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int i = t & 15, b0 = t >> 4;
-  const bool f32 = sm.b.tc.reduce_fp32 != 0 && i < nvals - 2;   // counts stay exact
-  double acc = 0.0;
-  float accf = 0.f;
-  if (i < nvals) {
-    for (int blk = b0; blk < nblk; blk += kThreads / 16) {
-      const double v = __ldcg(&partials[(size_t)blk * kPartialStride + i]);
-      if (f32) accf += (float)v;
-      else acc += v;
-    }
-  }
-  if (f32) acc = (double)accf;
-  acc += __shfl_xor_sync(kFull, acc, 16);
-  if (lane < 16 && i < nvals) sm.red_d[warp][i] = acc;
-  __syncthreads();
-  if (t < nvals) {
-    double r = 0.0;
+  static_assert(kWarps == 8, "the counts go to warp 7");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kMaxPer = 16;   // nblk <= 512 blocks: 16 per lane
+  const int nf = nvals - 2;     // FP64 values; nf <= 7
+  if (warp < nf) {
+    const int i = warp;
+    const bool f32 = sm.b.tc.reduce_fp32 != 0;
+    double v[kMaxPer];
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) r += sm.red_d[w][t];
-    out[t] = r;
+    for (int k = 0; k < kMaxPer; ++k) {
+      const int blk = lane + 32 * k;
+      v[k] = blk < nblk ? __ldcg(&partials[(size_t)blk * kPartialStride + i]) : 0.0;
+    }
+    double acc = 0.0;
+    float accf = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) {
+      if (32 * k >= nblk) break;
+      if (f32) accf += (float)v[k];
+      else acc += v[k];
+    }
+    if (f32) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) accf += __shfl_xor_sync(kFull, accf, off);
+      acc = (double)accf;
+    } else {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    }
+    if (lane == 0) out[i] = acc;
+  } else if (warp == kWarps - 1) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      unsigned long long n = 0;
+      for (int blk = lane; blk < nblk; blk += 32)
+        n += (unsigned long long)__double_as_longlong(
+            __ldcg(&partials[(size_t)blk * kPartialStride + nf + c]));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(kFull, n, off);
+      if (lane == 0) out[nf + c] = __longlong_as_double((long long)n);
+    }
   }
   __syncthreads();
 }
 
-// Barrier that also reduces the pass: the last block to arrive sums all block
-// partials in FP64 (fixed order, all its threads), publishes the totals and
-// then releases the others, which read the totals. Every thread of every block
-// gets the totals in sums[]. Bounded like grid_sync.
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Barrier that also reduces the pass: the block whose arrival completes
+// generation g sums all block partials in FP64 (fixed order, all its
+// threads), publishes the totals and then raises the release flag to g + 1;
+// the others wait for the flag and read the totals (thread 0, one round
+// trip). Every thread of every block gets the totals in sums[]. Bounded like
+// grid_sync.
 template <class Smem>
 __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const double* partials,
                                  int nvals, int nblk) {
+  const unsigned g = gen;
+  gen += 1;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-    sm.last = (arrived == (unsigned)nblk - 1) ? 1 : 0;
+    sm.last = (arrived + 1 == (g + 1) * (unsigned)nblk) ? 1 : 0;
   }
   __syncthreads();
-  const unsigned g = gen;
   if (sm.last) {
     reduce_partials(partials, nvals, sm.sums, nblk, sm);
     if (threadIdx.x < (unsigned)nvals) st->red_sums[threadIdx.x] = sm.sums[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
-      barrier_release(st, g);
+      __threadfence();
+      st_release_u32(&st->bar_rel, g + 1);
       sm.flag = 1;
     }
-  } else {
-    if (threadIdx.x == 0) {
-      sm.flag = barrier_wait(st, g) ? 1 : 0;
-      __threadfence();
+  } else if (threadIdx.x == 0) {
+    unsigned spins = 0;
+    int ok = 1;
+    while (ld_acquire(&st->bar_rel) < g + 1) {
+      if (++spins > kSpinLimit) {
+        atomicOr(&st->status, (int)kStatusTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
     }
-    __syncthreads();
-    if (threadIdx.x < (unsigned)nvals) sm.sums[threadIdx.x] = __ldcg(&st->red_sums[threadIdx.x]);
+    if (ok) {
+      for (int i = 0; i < nvals; ++i) sm.sums[i] = __ldcg(&st->red_sums[i]);
+    }
+    sm.flag = ok;
   }
-  gen = g + 1;
   __syncthreads();
   return sm.flag != 0;
 }
@@ -631,12 +781,29 @@ __device__ bool team_join(SolveState* st, int team_size, Smem& sm) {
   return sm.flag != 0;
 }
 
+// Squared distance from x to the box [lo, hi] (zero inside), the one form the
+// plan and every pass evaluate, so that they agree on each candidate.
+__device__ __forceinline__ float box_dist2(float4 x, float4 lo, float4 hi) {
+  const float dx = fmaxf(fmaxf(lo.x - x.x, x.x - hi.x), 0.f);
+  const float dy = fmaxf(fmaxf(lo.y - x.y, x.y - hi.y), 0.f);
+  const float dz = fmaxf(fmaxf(lo.z - x.z, x.z - hi.z), 0.f);
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
 // Plan of one cluster (one warp): transform its points, bounding box, cell
-// rows within the plan radius -> segments, candidate count.
+// rows within the plan radius -> segments, candidate count; then the
+// candidates themselves are read once and those farther than the plan radius
+// from the bounding box are filtered out (they cannot come within the cutoff
+// of any of the cluster's points while the plan is valid: a point within r_c
+// at the current pose lies within r_c + drift < plan radius of its plan-pose
+// position, which is inside the box). Per segment, the number of candidates
+// that pass gives the filtered offsets the work split and the passes use.
+// s_xs, s_pf, s_cnt: the warp's shared arrays (kMaxSeg + 1 entries).
 __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState* st, int c,
-                             int lane) {
+                             int lane, int* s_xs, int* s_pf, int* s_cnt) {
   const GridView& g = cfg->grids[b.level];
   const ClusterView& cv = cfg->clusters[b.level];
+  __syncwarp();   // the shared arrays of the warp's previous cluster are free
   const int p0 = cv.cstart[c];
   const int cs = cv.cstart[c + 1] - p0;
   const bool zv = lane < cs;
@@ -706,27 +873,93 @@ __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState*
     if (keep > 0) {
       sxs[idx] = xs;
       spf[idx] = total + incl - keep;
+      s_xs[idx] = xs;
+      s_pf[idx] = total + incl - keep;
     }
     nseg += __popc(m);
     total += __shfl_sync(kFull, incl, 31);
   }
   if (__any_sync(kFull, overflow) && lane == 0) atomicOr(&st->status, (int)kStatusSegOverflow);
+  nseg = min(nseg, kMaxSeg);
+  if (lane == 0) s_pf[nseg] = total;
+  for (int i = lane; i < nseg; i += 32) s_cnt[i] = 0;
+  __syncwarp();
+  // the filter: every candidate read once, four rounds of 32 loads in flight;
+  // a cluster with more than kFilterMax candidates is not filtered (its box is
+  // the whole space, every candidate passes): at the large lengthscales, where
+  // that happens, few candidates would be dropped and the plan is used once
+  const bool filt = total <= kFilterMax;
+  const float4 lo4 = filt ? make_float4(blo[0], blo[1], blo[2], 0.f)
+                          : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+  const float4 hi4 = filt ? make_float4(bhi[0], bhi[1], bhi[2], 0.f)
+                          : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+  if (!filt) {
+    for (int i = lane; i < nseg; i += 32) s_cnt[i] = s_pf[i + 1] - s_pf[i];
+  }
+  int seg = 0;
+  for (int u0 = 0; filt && u0 < total; u0 += 128) {
+    float4 xq[4];
+    int sq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = u0 + 32 * k + lane;
+      sq[k] = -1 - lane;   // distinct for every lane past the end
+      xq[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < total) {
+        while (s_pf[seg + 1] <= q) ++seg;
+        sq[k] = seg;
+        xq[k] = g.xyz[s_xs[seg] + (q - s_pf[seg])];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool pass = sq[k] >= 0 && box_dist2(xq[k], lo4, hi4) <= rp2;
+      const unsigned m = __ballot_sync(kFull, pass);
+      const unsigned grp = __match_any_sync(kFull, sq[k]);
+      const int n = __popc(grp & m);
+      if (sq[k] >= 0 && lane == __ffs(grp) - 1 && n > 0) atomicAdd(&s_cnt[sq[k]], n);
+    }
+  }
+  __syncwarp();
+  // filtered offsets of the segments (exclusive prefix over at most 64)
+  const int n0 = lane < nseg ? s_cnt[lane] : 0;
+  const int n1 = lane + 32 < nseg ? s_cnt[lane + 32] : 0;
+  int i0 = n0, i1 = n1;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v0 = __shfl_up_sync(kFull, i0, off);
+    const int v1 = __shfl_up_sync(kFull, i1, off);
+    if (lane >= off) {
+      i0 += v0;
+      i1 += v1;
+    }
+  }
+  const int t0 = __shfl_sync(kFull, i0, 31);
+  const int t1 = __shfl_sync(kFull, i1, 31);
+  int* sff = cfg->seg_fpref + (size_t)c * kMaxSeg;
+  if (lane < nseg) sff[lane] = i0 - n0;
+  if (lane + 32 < nseg) sff[lane + 32] = t0 + i1 - n1;
   if (lane == 0) {
-    cfg->cl_nseg[c] = min(nseg, kMaxSeg);
+    cfg->cl_nseg[c] = nseg;
     cfg->cl_cand[c] = total;
+    cfg->cl_fcand[c] = t0 + t1;
     cfg->cl_kept[c] = 0;
+    cfg->cl_box[2 * (size_t)c] = lo4;
+    cfg->cl_box[2 * (size_t)c + 1] = hi4;
   }
 }
 
 // Work of cluster c under the current plan, in pair-test units: staging the
-// cluster costs cost_cluster, each 32-candidate chunk its cs4 pair tests per
-// lane (cluster size padded to a multiple of 4) plus cost_chunk of per-chunk
-// overhead, plus (use_kept, once the plan's first gradient pass has counted
-// them) cost_kept per kept pair of the cluster, spread evenly over its chunks.
-// Chunk j starts at offset cost_cluster + j * k, k = the per-chunk cost.
+// cluster costs cost_cluster, each chunk of 32 filtered candidates its cs4
+// pair tests per lane (cluster size padded to a multiple of 4) plus
+// cost_chunk of per-chunk overhead, plus (use_kept, once the plan's first
+// gradient pass has counted them) cost_kept per kept pair of the cluster,
+// spread evenly over its chunks. Chunk j starts at offset cost_cluster + j * k,
+// k = the per-chunk cost; within a chunk, the overhead and the first group of
+// four source points come first, then one group (4 tests) after another.
 __device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const ClusterView& cv,
                                                   int c, int* k_out, bool use_kept) {
-  const int tc = __ldcg(&cfg->cl_cand[c]);
+  const int tc = __ldcg(&cfg->cl_fcand[c]);
   const int cs4 = ((cv.cstart[c + 1] - cv.cstart[c]) + 3) & ~3;
   const int nch = (tc + 31) >> 5;
   int k = cs4 + cfg->cost_chunk;
@@ -744,6 +977,7 @@ struct SolveSmem {
   float4 u[kWarps][NU][kClusterMax];
   int xs[kWarps][kMaxSeg];
   int pf[kWarps][kMaxSeg + 1];
+  int fpf[kWarps][kMaxSeg + 1];     // filtered offsets (the plan: per-segment counts)
   float red[kWarps][10];
   double red_d[kWarps][16];
   long long scan[kThreads];
@@ -759,11 +993,17 @@ struct SolveSmem {
   BlockCtx b;
 };
 
-// (cluster, chunk) of the first chunk whose work starts at or after s, for s
-// inside group `group` whose work starts at `base` (one warp). The chunk may
-// equal the cluster's chunk count, which means the next cluster's first chunk.
+// (cluster, chunk, group) of the first unit of work that starts at or after
+// s, for s inside group-of-clusters `group` whose work starts at `base` (one
+// warp). Units of a cluster whose work starts at e0: its staging
+// [e0, e0 + cost_cluster), then per chunk j (starting at e = e0 +
+// cost_cluster + j k) the unit of source group 0 at e (it carries the chunk's
+// overhead oh = k - cs4) and the unit of source group g > 0 at e + oh + 4 g.
+// The chunk may equal the cluster's chunk count, which means the next
+// cluster's first chunk.
 __device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, long long base,
-                       long long s, int lane, int* c_out, int* j_out, bool use_kept) {
+                       long long s, int lane, int* c_out, int* j_out, int* g_out,
+                       bool use_kept) {
   const int c = group * 32 + lane;
   long long w = 0;
   int kk = 4;
@@ -778,18 +1018,37 @@ __device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, lo
   const unsigned m = __ballot_sync(kFull, c < cv.ncl && w > 0 && s >= excl && s < excl + w);
   if (m) {
     const int src = __ffs(m) - 1;
+    const int cc = group * 32 + src;
     const long long e = __shfl_sync(kFull, excl, src) + cfg->cost_cluster;
     const int k4 = __shfl_sync(kFull, kk, src);
-    *c_out = group * 32 + src;
-    *j_out = s <= e ? 0 : (int)((s - e + k4 - 1) / k4);
+    const int cs4 = ((cv.cstart[cc + 1] - cv.cstart[cc]) + 3) & ~3;
+    const int oh = k4 - cs4;
+    int j = 0, gq = 0;
+    if (s > e) {
+      const long long r = s - e;
+      j = (int)(r / k4);
+      const int rr = (int)(r - (long long)j * k4);
+      if (rr > 0) {
+        gq = max(1, (rr - oh + 3) >> 2);   // the first g >= 1 with oh + 4 g >= rr
+        if (gq >= (cs4 >> 2)) {
+          ++j;
+          gq = 0;
+        }
+      }
+    }
+    *c_out = cc;
+    *j_out = j;
+    *g_out = gq;
   } else {
     *c_out = min(group * 32 + 32, cv.ncl);
     *j_out = 0;
+    *g_out = 0;
   }
 }
 
 // Place the block's warps on an even split of the plan's work: warp w owns the
-// chunks whose work starts in [floor(w TW/NW), floor((w+1) TW/NW)).
+// units (a chunk's source group) whose work starts in [floor(w TW/NW),
+// floor((w+1) TW/NW)).
 template <int DPS, int NU>
 __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid, Team team) {
   const ClusterView& cv = cfg->clusters[sm.b.level];
@@ -830,20 +1089,23 @@ __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid,
     const int q = 2 * warp + h;
     const long long w = (long long)team.rank * kWarps + warp + h;
     const long long s = TW > 0 ? (w * TW) / NW : 0;
-    int c, jj;
+    int c, jj, gg;
     if (TW == 0 || s >= TW || sm.bnd_group[q] < 0) {
       c = cv.ncl;   // past the end: no chunk
-      jj = 0;
+      jj = gg = 0;
     } else {
-      locate(cfg, cv, sm.bnd_group[q], sm.bnd_base[q], s, lane, &c, &jj, sm.b.use_kept != 0);
+      locate(cfg, cv, sm.bnd_group[q], sm.bnd_base[q], s, lane, &c, &jj, &gg,
+             sm.b.use_kept != 0);
     }
     if (lane == 0) {
       if (h == 0) {
         sm.b.w_c0[warp] = c;
         sm.b.w_j0[warp] = jj;
+        sm.b.w_g0[warp] = gg;
       } else {
         sm.b.w_c1[warp] = c;
         sm.b.w_j1[warp] = jj;
+        sm.b.w_g1[warp] = gg;
       }
     }
   }
@@ -902,8 +1164,9 @@ __device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, 
 
 // One 32-candidate chunk against the staged cluster: lane = candidate x'
 // (xp, features xf; padding points lie beyond every cutoff), inner loop over
-// the cluster's cs4 points (cluster size rounded up to 4; padding slots lie
-// beyond the cutoff too). FP32 pair arithmetic, one ex2.approx per pair.
+// the cluster's points [jlo, jhi) (multiples of 4, at most the cluster size
+// rounded up to 4; padding slots lie beyond the cutoff too). FP32 pair
+// arithmetic, one ex2.approx per pair.
 // Points are taken four at a time: the four distance tests first, then, if
 // any lane of the warp keeps any of the four pairs (one vote, so the branch
 // is uniform), the four pair bodies without branches, a rejected pair
@@ -912,10 +1175,10 @@ __device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, 
 // overlap.
 template <bool STEP, int DP, int MODE, int DPS, int NU>
 __device__ __forceinline__ void chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, float4 xp,
-                                            const float xf[DPS], int cs4, float rc2, float A,
-                                            float acc[7], unsigned& nnz) {
+                                            const float xf[DPS], int jlo, int jhi, float rc2,
+                                            float A, float acc[7], unsigned& nnz) {
   float W = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
-  for (int j0 = 0; j0 < cs4; j0 += 4) {
+  for (int j0 = jlo; j0 < jhi; j0 += 4) {
     float ex[4], ey[4], ez[4], d2[4];
     bool keep[4];
 #pragma unroll
@@ -989,27 +1252,49 @@ __device__ __forceinline__ void chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, fl
   }
 }
 
-// Segments of cluster c into the warp's shared arrays, and the segment that
-// holds candidate q0 (binary search over the candidate offsets).
+// A warp's range of work (BlockCtx::w_*).
+struct WarpRange {
+  int c0, j0, g0, c1, j1, g1;
+};
+
+__device__ __forceinline__ WarpRange warp_range(const BlockCtx& b, int warp) {
+  return WarpRange{b.w_c0[warp], b.w_j0[warp], b.w_g0[warp],
+                   b.w_c1[warp], b.w_j1[warp], b.w_g1[warp]};
+}
+
+// Chunks [jb, je] of cluster c (nch chunks) that hold work of the range.
+__device__ __forceinline__ bool range_chunks(const WarpRange& r, int c, int nch, int& jb, int& je) {
+  if (c < r.c0 || c > r.c1) return false;
+  jb = c == r.c0 ? r.j0 : 0;
+  je = nch - 1;
+  if (c == r.c1) je = min(je, r.g1 > 0 ? r.j1 : r.j1 - 1);
+  return jb <= je;
+}
+
+// Source groups [glo, ghi) of chunk j of cluster c (G groups) in the range.
+__device__ __forceinline__ void range_groups(const WarpRange& r, int c, int j, int G, int& glo,
+                                             int& ghi) {
+  glo = (c == r.c0 && j == r.j0) ? r.g0 : 0;
+  ghi = (c == r.c1 && j == r.j1) ? min(r.g1, G) : G;
+}
+
+// Segments of cluster c into the warp's shared arrays: first target index,
+// candidate offset (then tc) and filtered offset (then fc) of each segment.
 template <int DPS, int NU>
 __device__ __forceinline__ int load_segments(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
-                                             int lane, int c, int tc, int q0) {
+                                             int lane, int c, int tc, int fc) {
   const int nseg = __ldcg(&cfg->cl_nseg[c]);
   for (int i = lane; i < nseg; i += 32) {
     sm.xs[warp][i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
     sm.pf[warp][i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
+    sm.fpf[warp][i] = __ldcg(&cfg->seg_fpref[(size_t)c * kMaxSeg + i]);
   }
-  if (lane == 0) sm.pf[warp][nseg] = tc;
+  if (lane == 0) {
+    sm.pf[warp][nseg] = tc;
+    sm.fpf[warp][nseg] = fc;
+  }
   __syncwarp();
-  int lo = 0, hi = nseg;
-  if (q0 < tc) {
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (sm.pf[warp][mid] <= q0) lo = mid;
-      else hi = mid;
-    }
-  }
-  return lo;
+  return nseg;
 }
 
 // Candidate q of the staged cluster (padding beyond tc), advancing seg.
@@ -1029,6 +1314,51 @@ __device__ __forceinline__ float4 load_candidate(const GridView& g, SolveSmem<DP
   return xp;
 }
 
+// Cursor over the filtered candidates of the cluster whose segments are
+// staged: the next block of 32 candidates starts at candidate u; `skip`
+// filtered candidates are still to be dropped (they precede the range); seg
+// is this lane's segment; made counts the filtered candidates produced.
+struct FCursor {
+  int u, skip, seg, made;
+};
+
+// Cursor at filtered candidate f0 (< fc): the last segment whose filtered
+// offset is <= f0 (a segment that filters to nothing shares its offset with
+// the next one), from its first candidate.
+template <int DPS, int NU>
+__device__ __forceinline__ FCursor fcursor_at(const SolveSmem<DPS, NU>& sm, int warp, int nseg,
+                                              int f0) {
+  int lo = 0, hi = nseg;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (sm.fpf[warp][mid] <= f0) lo = mid;
+    else hi = mid;
+  }
+  FCursor cur;
+  cur.u = sm.pf[warp][lo];
+  cur.skip = f0 - sm.fpf[warp][lo];
+  cur.seg = lo;
+  cur.made = 0;
+  return cur;
+}
+
+// The block of candidates at cur.u (this lane's is xp) through the plan's
+// filter: the filtered index (counted from the cursor's start) of this lane's
+// candidate, or -1; the cursor moves to the next block.
+__device__ __forceinline__ int fplace(FCursor& cur, float4 xp, float4 lo, float4 hi, float rp2,
+                                      int lane, int tc) {
+  const bool pass = cur.u + lane < tc && box_dist2(xp, lo, hi) <= rp2;
+  const unsigned m = __ballot_sync(kFull, pass);
+  const int r = __popc(m & ((1u << lane) - 1u));
+  const int n = __popc(m);
+  const int d = min(cur.skip, n);
+  cur.skip -= d;
+  const int o = (pass && r >= d) ? cur.made + r - d : -1;
+  cur.made += n - d;
+  cur.u += 32;
+  return o;
+}
+
 // Kept pairs of cluster c counted by this warp, added to the plan's
 // per-cluster totals (one atomic per warp and cluster).
 __device__ __forceinline__ void add_kept(const SolveCfg* cfg, int c, unsigned kept, int lane) {
@@ -1038,92 +1368,136 @@ __device__ __forceinline__ void add_kept(const SolveCfg* cfg, int c, unsigned ke
   if (lane == 0 && c >= 0 && k) atomicAdd(&cfg->cl_kept[c], (int)k);
 }
 
+// Stage cluster c for the warp from global memory (raw centred source points
+// and features, transformed by stage_cluster).
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ __forceinline__ int stage_from_global(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm,
+                                                 const ClusterView& cv, int c, int warp,
+                                                 int lane) {
+  const int p0 = cv.cstart[c];
+  const int cs = cv.cstart[c + 1] - p0;
+  const bool zv = lane < cs;
+  float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+  float pf[DPS];
+#pragma unroll
+  for (int d = 0; d < DPS; ++d) pf[d] = 0.f;
+  if (zv) {
+    p = cfg->src.xyz[p0 + lane];
+#pragma unroll
+    for (int d = 0; d < DP; ++d)
+      pf[d] = load_feat<bf16_of(MODE)>(cfg->src.feat, (size_t)d * cfg->src.m_pad + p0 + lane);
+  }
+  stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, zv, p, pf);
+  return cs;
+}
+
 // One warp's share of a pair pass, streamed from global memory (L2): lane
-// sums in acc, counts in nnz / cand.
+// sums in acc, counts in nnz / cand. The filtered candidates of each chunk
+// are gathered through a ring of 64 entries in the warp's (otherwise unused)
+// cache region, with the next block of 32 candidates loading while the
+// current chunk runs.
 template <bool STEP, int DP, int MODE, int DPS, int NU>
 __device__ void pass_stream(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp, int lane,
-                            float acc[7], unsigned& nnz, unsigned& cand) {
+                            float* ring, float acc[7], unsigned& nnz, unsigned& cand) {
   const BlockCtx& b = sm.b;
   const GridView& g = cfg->grids[b.level];
   const ClusterView& cv = cfg->clusters[b.level];
   const float rc2 = b.rc2, A = b.A;
-  int c = b.w_c0[warp], jc = b.w_j0[warp];
-  const int c_end = b.w_c1[warp], j_end = b.w_j1[warp];
-  int loaded = -1, cs = 0, cs4 = 0, tc = 0, nch_c = 0, seg = 0;
-  float4 xp_next = make_float4(-kFar, -kFar, -kFar, 0.f);
-  float xf_next[DPS];
-#pragma unroll
-  for (int d = 0; d < DPS; ++d) xf_next[d] = 0.f;
-  bool have_next = false;
+  const float rp2 = b.rplan_f * b.rplan_f;
+  const WarpRange r = warp_range(b, warp);
   const bool collect = !STEP && b.collect_kept;
-  unsigned nnz0 = nnz;
-  for (;;) {
-    if (c != loaded) {
-      if (collect) {
-        add_kept(cfg, loaded, nnz - nnz0, lane);
-        nnz0 = nnz;
-      }
-      for (;;) {  // the next cluster that still has a chunk in this warp's range
-        if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) return;
-        tc = __ldcg(&cfg->cl_cand[c]);
-        nch_c = (tc + 31) >> 5;
-        if (jc < nch_c) break;
-        ++c;
-        jc = 0;
-      }
-      __syncwarp();   // every lane is done with the previous cluster's staging
-      const int p0 = cv.cstart[c];
-      cs = cv.cstart[c + 1] - p0;
-      const bool zv = lane < cs;
-      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      float pf[DPS];
+  float4* rxyz = reinterpret_cast<float4*>(ring);
+  float* rfeat = ring + 4 * 64;
+  for (int c = r.c0; c <= r.c1 && c < cv.ncl; ++c) {
+    const int tc = __ldcg(&cfg->cl_cand[c]);
+    const int fc = __ldcg(&cfg->cl_fcand[c]);
+    int jb, je;
+    if (!range_chunks(r, c, (fc + 31) >> 5, jb, je)) continue;
+    __syncwarp();   // every lane is done with the previous cluster
+    const int cs = stage_from_global<STEP, DP, MODE, DPS, NU>(cfg, sm, cv, c, warp, lane);
+    const int cs4 = (cs + 3) & ~3;
+    const int nseg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, fc);
+    const float4 lo = __ldcg(&cfg->cl_box[2 * (size_t)c]);
+    const float4 hi = __ldcg(&cfg->cl_box[2 * (size_t)c + 1]);
+    FCursor cur = fcursor_at<DPS, NU>(sm, warp, nseg, jb * 32);
+    const int want = min(fc, 32 * (je + 1)) - 32 * jb;
+    const unsigned nnz0 = nnz;
+    if (lo.x == -INFINITY) {
+      // an unfiltered cluster: chunk j holds candidates 32 j .. 32 j + 31,
+      // loaded straight into registers, the next chunk's while this one runs
+      float xfn[DPS];
+      float4 xpn = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, jb * 32 + lane, tc,
+                                                              cur.seg, xfn);
+      for (int j = jb; j <= je; ++j) {
+        const float4 xp = xpn;
+        float xf[DPS];
 #pragma unroll
-      for (int d = 0; d < DPS; ++d) pf[d] = 0.f;
-      if (zv) {
-        p = cfg->src.xyz[p0 + lane];
-#pragma unroll
-        for (int d = 0; d < DP; ++d)
-          pf[d] = load_feat<bf16_of(MODE)>(cfg->src.feat, (size_t)d * cfg->src.m_pad + p0 + lane);
+        for (int d = 0; d < DPS; ++d) xf[d] = xfn[d];
+        if (j < je)
+          xpn = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, (j + 1) * 32 + lane, tc,
+                                                           cur.seg, xfn);
+        int glo, ghi;
+        range_groups(r, c, j, cs4 >> 2, glo, ghi);
+        if (glo < ghi) {
+          const int jlo = 4 * glo, jhi = min(cs4, 4 * ghi);
+          if (j * 32 + lane < tc) cand += (unsigned)max(0, min(cs, jhi) - jlo);
+          chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, jlo, jhi, rc2, A, acc, nnz);
+        }
       }
-      stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, zv, p, pf);
-      cs4 = (cs + 3) & ~3;
-      loaded = c;
-      have_next = false;
-      seg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, jc * 32 + lane);
+      if (collect) add_kept(cfg, c, nnz - nnz0, lane);
+      continue;
     }
-    // candidate of chunk jc (prefetched during the previous chunk of the same
-    // cluster) and the prefetch of chunk jc + 1
-    float4 xp;
-    float xf[DPS];
-    if (have_next) {
-      xp = xp_next;
+    float xfn[DPS];
+    float4 xpn = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, cur.u + lane, tc,
+                                                            cur.seg, xfn);
+    int used = 0;
+    for (int j = jb; j <= je; ++j) {
+      const int cnt = min(32, want - used);
+      // place blocks until the chunk is complete (at most 63 entries are
+      // unread, so the ring never overwrites one)
+      while (cur.made - used < cnt && cur.u < tc) {
+        const int o = fplace(cur, xpn, lo, hi, rp2, lane, tc);
+        if (o >= 0) {
+          const int e = o & 63;
+          rxyz[e] = xpn;
 #pragma unroll
-      for (int d = 0; d < DPS; ++d) xf[d] = xf_next[d];
-    } else {
-      xp = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, jc * 32 + lane, tc, seg, xf);
+          for (int d = 0; d < DP; ++d) rfeat[d * 64 + e] = xfn[d];
+        }
+        if (cur.u < tc)
+          xpn = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, cur.u + lane, tc, cur.seg,
+                                                           xfn);
+      }
+      __syncwarp();
+      float4 xp = make_float4(-kFar, -kFar, -kFar, 0.f);
+      float xf[DPS];
+#pragma unroll
+      for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
+      const bool have = lane < cnt && used + lane < cur.made;
+      if (have) {
+        const int e = (used + lane) & 63;
+        xp = rxyz[e];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) xf[d] = rfeat[d * 64 + e];
+      }
+      __syncwarp();   // read before the next placement reuses the entries
+      int glo, ghi;
+      range_groups(r, c, j, cs4 >> 2, glo, ghi);
+      if (glo < ghi) {
+        const int jlo = 4 * glo, jhi = min(cs4, 4 * ghi);
+        if (have) cand += (unsigned)max(0, min(cs, jhi) - jlo);
+        chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, jlo, jhi, rc2, A, acc, nnz);
+      }
+      used += cnt;
     }
-    if (jc * 32 + lane < tc) cand += (unsigned)cs;
-    const bool last_of_range = (c == c_end && jc + 1 >= j_end);
-    have_next = (jc + 1 < nch_c) && !last_of_range;
-    if (have_next)
-      xp_next = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, (jc + 1) * 32 + lane, tc,
-                                                           seg, xf_next);
-    chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, cs4, rc2, A, acc, nnz);
-    if (last_of_range) {
-      if (collect) add_kept(cfg, loaded, nnz - nnz0, lane);
-      return;
-    }
-    if (++jc >= nch_c) {
-      ++c;
-      jc = 0;
-    }
+    if (collect) add_kept(cfg, c, nnz - nnz0, lane);
   }
 }
 
 // Shared-memory cache of a warp's share of the plan. A slot holds 32 points
 // (float4 xyz, then DP feature planes of 32 floats): either the raw centred
-// source points of a cluster (header kSlotCluster | cluster size) or the 32
-// candidates of a chunk (header = number of valid candidates; the rest are
+// source points of a cluster (header kSlotCluster | cluster size) or the
+// candidates of a chunk of filtered candidates (header: number of valid
+// candidates | first source group << 6 | end source group << 10; the rest are
 // padding points beyond every cutoff). Filled once per plan when the warp's
 // whole share fits, so that the passes of every iteration that reuses the
 // plan (at the lengthscale floor, most of the solve) read no global memory.
@@ -1141,22 +1515,13 @@ __device__ void fill_cache(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp
   const BlockCtx& b = sm.b;
   const GridView& g = cfg->grids[b.level];
   const ClusterView& cv = cfg->clusters[b.level];
-  const int c0 = b.w_c0[warp], j0 = b.w_j0[warp];
-  const int c_end = b.w_c1[warp], j_end = b.w_j1[warp];
+  const WarpRange r = warp_range(b, warp);
+  const float rp2 = b.rplan_f * b.rplan_f;
   // count the slots the share needs
   int need = 0;
-  {
-    int c = c0, jc = j0;
-    for (;;) {
-      if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) break;
-      const int nch = (__ldcg(&cfg->cl_cand[c]) + 31) >> 5;
-      if (jc < nch) {
-        const int jl = (c == c_end) ? min(nch, j_end) : nch;
-        need += 1 + (jl - jc);
-      }
-      ++c;
-      jc = 0;
-    }
+  for (int c = r.c0; c <= r.c1 && c < cv.ncl; ++c) {
+    int jb, je;
+    if (range_chunks(r, c, (__ldcg(&cfg->cl_fcand[c]) + 31) >> 5, jb, je)) need += 2 + je - jb;
   }
   if (need > min(slots, kCacheSlots)) {
     if (lane == 0) sm.cache_n[warp] = -1;
@@ -1165,45 +1530,61 @@ __device__ void fill_cache(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp
   }
   float* base = cache + (size_t)warp * slots * slot_floats<DP>();
   int n = 0;
-  int c = c0, jc = j0;
-  for (;;) {
-    if (c > c_end || (c == c_end && jc >= j_end) || c >= cv.ncl) break;
+  for (int c = r.c0; c <= r.c1 && c < cv.ncl; ++c) {
     const int tc = __ldcg(&cfg->cl_cand[c]);
-    const int nch = (tc + 31) >> 5;
-    if (jc < nch) {
-      const int jl = (c == c_end) ? min(nch, j_end) : nch;
-      const int p0 = cv.cstart[c];
-      const int cs = cv.cstart[c + 1] - p0;
-      float* sl = base + (size_t)n * slot_floats<DP>();
-      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (lane < cs) p = cfg->src.xyz[p0 + lane];
-      reinterpret_cast<float4*>(sl)[lane] = p;
+    const int fc = __ldcg(&cfg->cl_fcand[c]);
+    int jb, je;
+    if (!range_chunks(r, c, (fc + 31) >> 5, jb, je)) continue;
+    const int p0 = cv.cstart[c];
+    const int cs = cv.cstart[c + 1] - p0;
+    float* sl = base + (size_t)n * slot_floats<DP>();
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < cs) p = cfg->src.xyz[p0 + lane];
+    reinterpret_cast<float4*>(sl)[lane] = p;
 #pragma unroll
-      for (int d = 0; d < DP; ++d)
-        sl[128 + d * 32 + lane] =
-            lane < cs ? load_feat<bf16_of(MODE)>(cfg->src.feat, (size_t)d * cfg->src.m_pad + p0 + lane)
-                      : 0.f;
-      if (lane == 0) {
-        sm.cache_hdr[warp][n] = (unsigned short)(kSlotCluster | cs);
-        sm.cache_cl[warp][n] = c;
-      }
-      ++n;
-      int seg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, jc * 32 + lane);
-      for (int k = jc; k < jl; ++k) {
-        float xf[DPS];
-        const float4 xp =
-            load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, k * 32 + lane, tc, seg, xf);
-        float* sk = base + (size_t)n * slot_floats<DP>();
-        reinterpret_cast<float4*>(sk)[lane] = xp;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) sk[128 + d * 32 + lane] = xf[d];
-        if (lane == 0) sm.cache_hdr[warp][n] = (unsigned short)min(32, tc - k * 32);
-        ++n;
-      }
-      __syncwarp();   // the segment arrays are reused by the next cluster
+    for (int d = 0; d < DP; ++d)
+      sl[128 + d * 32 + lane] =
+          lane < cs ? load_feat<bf16_of(MODE)>(cfg->src.feat, (size_t)d * cfg->src.m_pad + p0 + lane)
+                    : 0.f;
+    if (lane == 0) {
+      sm.cache_hdr[warp][n] = (unsigned short)(kSlotCluster | cs);
+      sm.cache_cl[warp][n] = c;
     }
-    ++c;
-    jc = 0;
+    ++n;
+    const int nseg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, fc);
+    const float4 lo = __ldcg(&cfg->cl_box[2 * (size_t)c]);
+    const float4 hi = __ldcg(&cfg->cl_box[2 * (size_t)c + 1]);
+    FCursor cur = fcursor_at<DPS, NU>(sm, warp, nseg, jb * 32);
+    const int want = min(fc, 32 * (je + 1)) - 32 * jb;
+    float* s0 = base + (size_t)n * slot_floats<DP>();
+    while (cur.made < want && cur.u < tc) {
+      float xf[DPS];
+      const float4 xp =
+          load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, cur.u + lane, tc, cur.seg, xf);
+      const int o = fplace(cur, xp, lo, hi, rp2, lane, tc);
+      if (o >= 0 && o < want) {
+        float* sk = s0 + (size_t)(o >> 5) * slot_floats<DP>();
+        reinterpret_cast<float4*>(sk)[o & 31] = xp;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) sk[128 + d * 32 + (o & 31)] = xf[d];
+      }
+    }
+    const int nchk = je - jb + 1;
+    for (int o = min(cur.made, want) + lane; o < 32 * nchk; o += 32) {   // padding
+      float* sk = s0 + (size_t)(o >> 5) * slot_floats<DP>();
+      reinterpret_cast<float4*>(sk)[o & 31] = make_float4(-kFar, -kFar, -kFar, 0.f);
+#pragma unroll
+      for (int d = 0; d < DP; ++d) sk[128 + d * 32 + (o & 31)] = 0.f;
+    }
+    if (lane <= je - jb) {
+      const int j = jb + lane;
+      int glo, ghi;
+      range_groups(r, c, j, ((cs + 3) & ~3) >> 2, glo, ghi);
+      const int cnt = min(32, want - 32 * lane);
+      sm.cache_hdr[warp][n + lane] = (unsigned short)(cnt | (glo << 6) | (ghi << 10));
+    }
+    n += nchk;
+    __syncwarp();   // the segment arrays are reused by the next cluster
   }
   if (lane == 0) sm.cache_n[warp] = (short)n;
   __syncwarp();
@@ -1234,13 +1615,15 @@ __device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
         nnz0 = nnz;
       }
       __syncwarp();   // every lane is done with the previous cluster
-      cs = (int)(h & 0xff);
+      cs = (int)(h & 0x3f);
       stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, lane < cs, p, f);
       cs4 = (cs + 3) & ~3;
       __syncwarp();
     } else {
-      if (lane < (int)h) cand += (unsigned)cs;
-      chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, p, f, cs4, rc2, A, acc, nnz);
+      const int cnt = (int)(h & 0x3f);
+      const int jlo = 4 * (int)((h >> 6) & 0xf), jhi = min(cs4, 4 * (int)((h >> 10) & 0xf));
+      if (lane < cnt) cand += (unsigned)max(0, min(cs, jhi) - jlo);
+      chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, p, f, jlo, jhi, rc2, A, acc, nnz);
     }
   }
   if (collect) add_kept(cfg, cur, nnz - nnz0, lane);
@@ -1248,18 +1631,20 @@ __device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
 
 template <bool STEP, int DP, int MODE, int DPS, int NU>
 __device__ __forceinline__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp,
-                                          int lane, const float* cache, int slots, float acc[7],
+                                          int lane, float* cache, int slots, float acc[7],
                                           unsigned& nnz, unsigned& cand) {
   if (sm.cache_n[warp] >= 0)
     pass_cached<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots, acc, nnz, cand);
   else
-    pass_stream<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, acc, nnz, cand);
+    pass_stream<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane,
+                                         cache + (size_t)warp * slots * slot_floats<DP>(), acc,
+                                         nnz, cand);
 }
 
 // One pass over the block's warps, then the block partial (fixed order).
 template <bool STEP, int DP, int MODE, int DPS, int NU>
 __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials, int rank,
-                         const float* cache, int slots) {
+                         float* cache, int slots) {
   constexpr int NACC = STEP ? 5 : 7;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float acc[7];
@@ -1297,7 +1682,7 @@ __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* pa
       unsigned long long n = 0;
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) n += __float_as_uint(sm.red[w][lane]);
-      s = (double)n;
+      s = __longlong_as_double((long long)n);   // a count: its bits, summed as an integer
     }
     partials[(size_t)rank * kPartialStride + lane] = s;
   }
@@ -1390,7 +1775,8 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     if (replan || rebalance) {
       const ClusterView& cv = cfg->clusters[sm.b.level];
       if (replan) {
-        for (long long c = gw; c < cv.ncl; c += NW) plan_cluster(cfg, sm.b, st, (int)c, lane);
+        for (long long c = gw; c < cv.ncl; c += NW)
+          plan_cluster(cfg, sm.b, st, (int)c, lane, sm.xs[warp], sm.pf[warp], sm.fpf[warp]);
         if (!grid_sync(st, gen, &sm.flag, team.size)) break;
       }
       if (tid == 0) sm.b.use_kept = rebalance;
@@ -1628,6 +2014,11 @@ const CacheCfg& cache_cfg() {
     const int slot_bytes = 4 * 32 * (4 + DP);
     const int avail = smem_sm / CVO_SOLVE_MIN_BLOCKS - reserved - (int)fa.sharedSizeBytes;
     c.slots = std::max(0, std::min(kCacheSlots, avail / (kWarps * slot_bytes)));
+    // the streamed passes gather candidates through two slots of each warp
+    if (c.slots < 2) {
+      c.err = cudaErrorInvalidConfiguration;
+      return c;
+    }
     c.bytes = c.slots * kWarps * slot_bytes;
     if (c.bytes > 0) {
       c.err = cudaFuncSetAttribute(solve_kernel<DP, MODE>,

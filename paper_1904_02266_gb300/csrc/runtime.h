@@ -67,6 +67,9 @@ struct Plan {
   int* seg_pref = nullptr;
   int* cl_nseg = nullptr;
   int* cl_cand = nullptr;
+  int* seg_fpref = nullptr;
+  int* cl_fcand = nullptr;
+  float4* cl_box = nullptr;
   int* cl_kept = nullptr;
   long long* group_agg = nullptr;
   int cap_iters = 0, cap_ncl = 0;
