@@ -361,6 +361,9 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
     ic[k].rc2 = (float)rc2;
     ic[k].rprune = (float)(std::sqrt(rc2) * 1.001);
     ic[k].level = level_of[k];
+    ic[k].filter = (mode == kModeEval ||
+                    (k + 1 < ells.size() && ells[k + 1] == ell && level_of[k + 1] == level_of[k]))
+                       ? 1 : 0;
   }
   cfg.src.xyz = s->zs;
   cfg.src.feat = s->zf;

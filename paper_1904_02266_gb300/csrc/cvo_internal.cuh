@@ -67,6 +67,9 @@ struct IterConst {
   float rc2;               // cutoff radius squared
   float rprune;            // traversal radius (r_c widened by 1e-3 relative)
   int level;               // grid / cluster level
+  int filter;              // 1: a plan built at this iteration filters its candidates (the
+                           //   next iteration keeps the lengthscale, so the plan is reused;
+                           //   or an evaluation)
 };
 
 // Constant for one solve plan (device memory).

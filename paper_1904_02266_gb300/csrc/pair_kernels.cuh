@@ -140,7 +140,7 @@ struct BlockCtx {
   double S[5];
   double t, t_prev;
   double ell, inv_l2, r_plan, plan_ell;
-  int k, level, plan_level;
+  int k, level, plan_level, plan_filter;
   int need_plan, done, converged, fallback, no_ascent, have_t_prev;
   int use_kept, collect_kept, rebalance;   // kept-pair weighting of the work split
   unsigned long long nnz_total, cand_total, nnz_grad, cand_grad;
@@ -218,6 +218,7 @@ __device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
       b.need_plan = 1;
       b.plan_level = ic.level;
       b.plan_ell = ic.ell;
+      b.plan_filter = ic.filter;
       b.r_plan = need * (1.0 + kSkin);
       b.rplan_f = (float)b.r_plan;
     }
@@ -884,11 +885,12 @@ __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState*
   if (lane == 0) s_pf[nseg] = total;
   for (int i = lane; i < nseg; i += 32) s_cnt[i] = 0;
   __syncwarp();
-  // the filter: every candidate read once, four rounds of 32 loads in flight;
-  // a cluster with more than kFilterMax candidates is not filtered (its box is
-  // the whole space, every candidate passes): at the large lengthscales, where
-  // that happens, few candidates would be dropped and the plan is used once
-  const bool filt = total <= kFilterMax;
+  // the filter: every candidate read once, four rounds of 32 loads in flight.
+  // Only a plan that will be reused (the next iteration keeps the lengthscale)
+  // is filtered, and only its clusters of at most kFilterMax candidates; the
+  // others get the whole space as their box (every candidate passes): a plan
+  // used for one iteration does not repay the extra read
+  const bool filt = b.plan_filter != 0 && total <= kFilterMax;
   const float4 lo4 = filt ? make_float4(blo[0], blo[1], blo[2], 0.f)
                           : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
   const float4 hi4 = filt ? make_float4(bhi[0], bhi[1], bhi[2], 0.f)
@@ -1743,6 +1745,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     b.k = 0;
     b.level = 0;
     b.plan_level = -1;
+    b.plan_filter = 0;
     b.need_plan = 1;
     b.done = cfg->max_iters <= 0 ? 1 : 0;
     b.converged = b.fallback = b.no_ascent = b.have_t_prev = 0;
