@@ -183,9 +183,11 @@ __device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
   // ell shrinks a fresh, tighter plan costs less than the extra candidates
   bool replan = b.need_plan || ic.level != b.plan_level || ic.ell != b.plan_ell;
   if (!replan) {
-    const double d = v - (c == 3 ? b.Tp[r] : b.Rp[3 * r + c]);
-    const double sq = lane < 12 ? d * d : 0.0;
-    double sr = c < 3 ? sq : 0.0, st = c == 3 ? sq : 0.0;
+    // the differences in FP64, their squares summed in FP32 (the 1e-5
+    // relative margin below covers FP32 rounding)
+    const float d = (float)(v - (c == 3 ? b.Tp[r] : b.Rp[3 * r + c]));
+    const float sq = lane < 12 ? d * d : 0.0f;
+    float sr = c < 3 ? sq : 0.0f, st = c == 3 ? sq : 0.0f;
 #pragma unroll
     for (int off = 8; off > 0; off >>= 1) {
       sr += __shfl_xor_sync(kFull, sr, off);
@@ -194,7 +196,7 @@ __device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
     sr = __shfl_sync(kFull, sr, 0);
     st = __shfl_sync(kFull, st, 0);
     // |dR z + dT| <= |dR|_F |z| + |dT| for every source point, |z| <= r_src
-    const double drift = ((double)sqrtf((float)sr) * b.tc.src_radius + (double)sqrtf((float)st)) *
+    const double drift = ((double)sqrtf(sr) * b.tc.src_radius + (double)sqrtf(st)) *
                              (1.0 + 1e-5) + 1e-6 * need;
     replan = (need + drift > b.r_plan) || (b.r_plan > kLoose * (need + drift));
   }
@@ -264,93 +266,107 @@ __device__ __forceinline__ double sqrt64(double x) {
 // start takes two steps; a far one (the FP32 form loses the small roots of a
 // cubic whose roots differ by orders of magnitude) a few more.
 __device__ bool first_maximiser(double c0, double c1, double c2, double c3, double* t_out) {
-  const double s = fmax(fmax(fabs(c0), fabs(c1)), fmax(fabs(c2), fabs(c3)));
-  if (!(s > 0.0) || !isfinite(s)) return false;
-  // 2^-e with s = m 2^e, m in [0.5, 1): built from the exponent field of s
-  // (s is finite and positive; subnormal s are scaled twice)
-  double sc = 1.0;
-  double ss = s;
-  if (ss < 0x1p-1000) {
-    sc = 0x1p+1000;
-    ss *= sc;
+  // the largest exponent field among the coefficients (integer work: FP64
+  // instructions are the scarce resource here)
+  const int e_max = max(max((__double2hiint(c0) >> 20) & 0x7ff, (__double2hiint(c1) >> 20) & 0x7ff),
+                        max((__double2hiint(c2) >> 20) & 0x7ff, (__double2hiint(c3) >> 20) & 0x7ff));
+  if (e_max == 0x7ff) return false;   // an infinity or a NaN
+  double sc;
+  if (e_max >= 2 && e_max <= 2044) {
+    // 2^(1022 - e_max): the largest magnitude lands in [0.5, 1)
+    sc = __hiloint2double((2045 - e_max) << 20, 0);
+  } else {
+    const double s = fmax(fmax(fabs(c0), fabs(c1)), fmax(fabs(c2), fabs(c3)));
+    if (!(s > 0.0)) return false;
+    // 2^-e with s = m 2^e, m in [0.5, 1) (subnormal s are scaled twice)
+    sc = 1.0;
+    double ss = s;
+    if (ss < 0x1p-1000) {
+      sc = 0x1p+1000;
+      ss *= sc;
+    }
+    const int ex = min(1000, ((__double2hiint(ss) >> 20) & 0x7ff) - 1022);
+    sc *= __hiloint2double((1023 - ex) << 20, 0);
   }
-  const int ex = min(1000, ((__double2hiint(ss) >> 20) & 0x7ff) - 1022);
-  sc *= __hiloint2double((1023 - ex) << 20, 0);
   c0 *= sc;
   c1 *= sc;
   c2 *= sc;
   c3 *= sc;
-  if (fabs(c3) < 1e-30) c3 = 0.0;
-  if (fabs(c2) < 1e-30) c2 = 0.0;
-  // start: a root of the cubic from the closed form in FP32 (any root; the
-  // bracket below decides which one is wanted); a negligible cubic term is
+  // start: a root of the cubic from the closed form, all in FP32 on the
+  // scaled coefficients (any root; the checks below decide whether it is the
+  // wanted one), refined by two FP32 Newton steps; a negligible cubic term is
   // left out of the start only
-  double t32 = -1.0;
-  if (fabs(c3) <= 1e-12) {
-    if (fabs(c2) <= 1e-12) {
-      if (c1 < 0.0) t32 = (double)(-(float)c0 / (float)c1);
+  const float f0 = (float)c0, f1 = (float)c1, f2 = (float)c2, f3 = (float)c3;
+  float ts = -1.0f;
+  if (fabsf(f3) <= 1e-12f) {
+    if (fabsf(f2) <= 1e-12f) {
+      if (f1 < 0.0f) ts = -f0 / f1;
     } else {
-      const double disc = c1 * c1 - 4.0 * c2 * c0;
-      if (disc >= 0.0) {
-        const float qf = -0.5f * ((float)c1 + copysignf(sqrtf((float)disc), (float)c1));
-        const float ra = qf / (float)c2, rb = (float)c0 / qf;
-        t32 = (double)((c2 < 0.0) ? fmaxf(ra, rb) : fminf(ra, rb));
+      const float disc = fmaf(f1, f1, -4.0f * f2 * f0);
+      if (disc >= 0.0f) {
+        const float qf = -0.5f * (f1 + copysignf(sqrtf(disc), f1));
+        const float ra = qf / f2, rb = f0 / qf;
+        ts = (f2 < 0.0f) ? fmaxf(ra, rb) : fminf(ra, rb);
       }
     }
   } else {
-    const double r3 = rcp64(c3);
-    const double B = c2 * r3, C = c1 * r3, D = c0 * r3;
-    const double B3 = B * (1.0 / 3.0);
-    const double p = fma(-B, B3, C);
-    const double q = fma((2.0 / 27.0) * B * B, B, fma(-B3, C, D));
-    const double disc = fma(0.25 * q, q, (1.0 / 27.0) * p * p * p);
-    const float pf = (float)p, qf = (float)q, B3f = (float)B3;
-    if (disc > 0.0) {
-      const float u = -copysignf(cbrtf(0.5f * fabsf(qf) + sqrtf((float)disc)), qf);
-      t32 = (double)((u != 0.0f ? u - pf / (3.0f * u) : 0.0f) - B3f);
-    } else if (p < 0.0) {
+    const float r3 = 1.0f / f3;
+    const float B = f2 * r3, C = f1 * r3, D = f0 * r3;
+    const float B3 = B * (1.0f / 3.0f);
+    const float p = fmaf(-B, B3, C);
+    const float q = fmaf((2.0f / 27.0f) * B * B, B, fmaf(-B3, C, D));
+    const float disc = fmaf(0.25f * q, q, (1.0f / 27.0f) * p * p * p);
+    if (disc > 0.0f) {
+      const float u = -copysignf(cbrtf(0.5f * fabsf(q) + sqrtf(disc)), q);
+      ts = (u != 0.0f ? u - p / (3.0f * u) : 0.0f) - B3;
+    } else if (p < 0.0f) {
       // roots m cos(phi - 2 pi k / 3) - B/3: k = 0 largest, k = 1 middle, k = 2 smallest
-      const float m = 2.0f * sqrtf(-pf * (1.0f / 3.0f));
-      const float arg = fminf(1.0f, fmaxf(-1.0f, 3.0f * qf / (pf * m)));
+      const float m = 2.0f * sqrtf(-p * (1.0f / 3.0f));
+      const float arg = fminf(1.0f, fmaxf(-1.0f, 3.0f * q / (p * m)));
       const float phi = acosf(arg) * (1.0f / 3.0f);
       const float two_pi_3 = 2.09439510239319549f;
       // the hardware cosine is accurate enough for a start
-      const float rk[3] = {m * __cosf(phi) - B3f, m * __cosf(phi - two_pi_3) - B3f,
-                           m * __cosf(phi - 2.0f * two_pi_3) - B3f};
+      const float rk[3] = {m * __cosf(phi) - B3, m * __cosf(phi - two_pi_3) - B3,
+                           m * __cosf(phi - 2.0f * two_pi_3) - B3};
       // the smallest positive one that G' crosses from + to - (as far as FP32 tells)
-      t32 = -1.0;
       for (int k = 0; k < 3; ++k) {
-        const double tk = (double)rk[k];
-        if (tk > 0.0 && fma(fma(3.0 * c3, tk, 2.0 * c2), tk, c1) < 0.0 && (t32 < 0.0 || tk < t32))
-          t32 = tk;
+        const float tk = rk[k];
+        if (tk > 0.0f && fmaf(fmaf(3.0f * f3, tk, 2.0f * f2), tk, f1) < 0.0f && (ts < 0.0f || tk < ts))
+          ts = tk;
       }
     }
   }
-  // fast path: Newton from the closed-form root; accepted when it converges
-  // (a first step below 1e-7 t: the start was FP32-accurate and one step
-  // squares that error) and G'' < 0 on [0, t] (then G' falls from c0 > 0 over
-  // [0, t], so t is its first root and a + -> - crossing)
-  if (isfinite(t32) && t32 > 0.0) {
-    double t = t32;
-    bool conv = false;
-    for (int it = 0; it < 3; ++it) {
-      const double f = fma(fma(fma(c3, t, c2), t, c1), t, c0);
-      const double fp = fma(fma(3.0 * c3, t, 2.0 * c2), t, c1);
-      if (!(fp < 0.0) || !isfinite(fp)) break;
-      const double tn = fma(-f, rcp64(fp), t);
-      if (!(tn > 0.0) || !isfinite(tn)) break;
-      conv = fabs(tn - t) <= (it == 0 ? 1e-7 : 1e-13) * tn;
-      t = tn;
-      if (conv) break;
-    }
-    // G''(0) = c1 < 0, G''(t) < 0, and for concave G'' (c3 < 0) with its
-    // vertex -c2 / (3 c3) inside (0, t), the vertex value c1 - c2^2 / (3 c3) < 0
-    if (conv && c1 < 0.0 && fma(fma(3.0 * c3, t, 2.0 * c2), t, c1) < 0.0 &&
-        (!(c3 < 0.0 && c2 > 0.0 && c2 < -3.0 * c3 * t) || 3.0 * c1 * c3 > c2 * c2)) {
-      *t_out = t;
-      return true;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float ff = fmaf(fmaf(fmaf(f3, ts, f2), ts, f1), ts, f0);
+    const float fd = fmaf(fmaf(3.0f * f3, ts, 2.0f * f2), ts, f1);
+    const float tn = ts - ff / fd;
+    if (fd < 0.0f && tn > 0.0f && isfinite(tn)) ts = tn;
+  }
+  const double t32 = (double)ts;
+  // fast path: one FP64 Newton step from that start, accepted when it moves t
+  // by at most 1e-6 t (the step squares the start's error) and G'' < 0 on
+  // [0, t] (then G' falls from c0 > 0 over [0, t], so t is its first root and
+  // a + -> - crossing)
+  if (ts > 0.0f && isfinite(ts)) {
+    const double f = fma(fma(fma(c3, t32, c2), t32, c1), t32, c0);
+    const double fp = fma(fma(3.0 * c3, t32, 2.0 * c2), t32, c1);
+    if (fp < 0.0) {
+      // 1/fp from FP32 and one FP64 Newton step (an fp outside FP32's range
+      // gives a non-finite t, which the checks reject)
+      const double t = fma(-f, recip_refined(fp), t32);
+      // G''(0) = c1 < 0, G''(t) < 0, and for concave G'' (c3 < 0) with its
+      // vertex -c2 / (3 c3) inside (0, t), the vertex value c1 - c2^2 / (3 c3) < 0
+      if (t > 0.0 && isfinite(t) && fabs(t - t32) <= 1e-6 * t && c1 < 0.0 &&
+          fma(fma(3.0 * c3, t, 2.0 * c2), t, c1) < 0.0 &&
+          (!(c3 < 0.0 && c2 > 0.0 && c2 < -3.0 * c3 * t) || 3.0 * c1 * c3 > c2 * c2)) {
+        *t_out = t;
+        return true;
+      }
     }
   }
+  if (fabs(c3) < 1e-30) c3 = 0.0;
+  if (fabs(c2) < 1e-30) c2 = 0.0;
   // positive critical points of G', ascending
   double e0 = -1.0, e1 = -1.0;
   if (c3 != 0.0) {
