@@ -105,6 +105,8 @@ void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
   dev_free(ctx, p->cl_fcand);
   dev_free(ctx, p->cl_box);
   dev_free(ctx, p->cl_kept);
+  dev_free(ctx, p->ch_act);
+  dev_free(ctx, p->cl_act);
   dev_free(ctx, p->group_agg);
   release_bytes(ctx, p->bytes);
   p->d_cfg = nullptr;
@@ -115,6 +117,8 @@ void free_plan_buffers(cvo_ctx* ctx, Plan* p) {
   p->seg_xs = p->seg_pref = p->cl_nseg = p->cl_cand = p->cl_kept = nullptr;
   p->seg_fpref = p->cl_fcand = nullptr;
   p->cl_box = nullptr;
+  p->ch_act = nullptr;
+  p->cl_act = nullptr;
   p->group_agg = nullptr;
   p->bytes = 0;
   p->cap_iters = p->cap_ncl = 0;
@@ -291,6 +295,8 @@ int reserve_plan(cvo_ctx* ctx, Plan* p, int iters, int ncl, int nblocks) {
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_fcand, sizeof(int) * ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_box, sizeof(float4) * 2 * (size_t)ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_kept, sizeof(int) * ncl, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->ch_act, sizeof(unsigned) * 32 * (size_t)ncl, &p->bytes);
+  if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->cl_act, sizeof(int) * ncl, &p->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&p->group_agg, sizeof(long long) * ng, &p->bytes);
   if (rc != CVO_OK) {
     free_plan_buffers(ctx, p);
@@ -378,6 +384,8 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   cfg.cl_fcand = p->cl_fcand;
   cfg.cl_box = p->cl_box;
   cfg.cl_kept = p->cl_kept;
+  cfg.ch_act = p->ch_act;
+  cfg.cl_act = p->cl_act;
   cfg.group_agg = p->group_agg;
   cfg.src_radius = s->radius;
   cfg.cost_chunk = prm.cost_chunk;

@@ -89,6 +89,9 @@ struct SolveCfg {
   float4* cl_box;          // per cluster: bounding box of its transformed points at the
                            //   plan pose (lo, hi)
   int* cl_kept;            // kept pairs per cluster in the first gradient pass of a plan
+  unsigned* ch_act;        // per cluster, 32 words: bit g of word j is set when source group g
+                           //   of chunk j kept a pair in the plan's first gradient pass
+  int* cl_act;             // per cluster: the number of such bits
   long long* group_agg;    // work of each group of 32 consecutive clusters
   double src_radius;       // max |z'| over the centred source (bounds pose drift)
   int cost_chunk;          // work model: a chunk costs cs4 + cost_chunk pair tests,

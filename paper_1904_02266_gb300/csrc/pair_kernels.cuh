@@ -63,6 +63,12 @@ constexpr unsigned long long kJoinLimitNs = 60ull * 1000 * 1000 * 1000;
 constexpr double kSkin = 0.10;              // plan radius margin (fraction of the cutoff)
 constexpr double kLoose = 1.25;             // replan when the plan radius exceeds this factor
 constexpr int kFilterMax = 1024;            // candidates of a cluster the plan filters at most
+constexpr int kActChunks = 32;              // chunks per cluster whose source-group activity is kept
+#ifndef CVO_COST_ACTIVE
+#define CVO_COST_ACTIVE 12
+#endif
+// work model: the pair bodies of a source group that kept a pair, in pair-test units
+constexpr int kCostActive = CVO_COST_ACTIVE;
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -143,6 +149,7 @@ struct BlockCtx {
   int k, level, plan_level, plan_filter;
   int need_plan, done, converged, fallback, no_ascent, have_t_prev;
   int use_kept, collect_kept, rebalance;   // kept-pair weighting of the work split
+  int use_act;                             // the split weighs source groups by their activity
   unsigned long long nnz_total, cand_total, nnz_grad, cand_grad;
   float R[9], T[3];       // FP32 centred pose: z~' = R z' + T
   float om[3], vc[3];     // unit step direction (centred frame)
@@ -957,7 +964,9 @@ __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState*
   int* sff = cfg->seg_fpref + (size_t)c * kMaxSeg;
   if (lane < nseg) sff[lane] = i0 - n0;
   if (lane + 32 < nseg) sff[lane + 32] = t0 + i1 - n1;
+  cfg->ch_act[(size_t)c * kActChunks + lane] = 0u;
   if (lane == 0) {
+    cfg->cl_act[c] = 0;
     cfg->cl_nseg[c] = nseg;
     cfg->cl_cand[c] = total;
     cfg->cl_fcand[c] = t0 + t1;
@@ -975,8 +984,13 @@ __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState*
 // spread evenly over its chunks. Chunk j starts at offset cost_cluster + j * k,
 // k = the per-chunk cost; within a chunk, the overhead and the first group of
 // four source points come first, then one group (4 tests) after another.
+// With use_act (a reused plan, once its first gradient pass has recorded
+// which source groups of which chunks kept a pair), each such group costs
+// kCostActive more (its pair bodies); chunks beyond the recorded ones count
+// every group as active.
 __device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const ClusterView& cv,
-                                                  int c, int* k_out, bool use_kept) {
+                                                  int c, int* k_out, bool use_kept,
+                                                  bool use_act) {
   const int tc = __ldcg(&cfg->cl_fcand[c]);
   const int cs4 = ((cv.cstart[c + 1] - cv.cstart[c]) + 3) & ~3;
   const int nch = (tc + 31) >> 5;
@@ -984,7 +998,12 @@ __device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const Clu
   if (use_kept && nch > 0)
     k += (int)(cfg->cost_kept * (float)__ldcg(&cfg->cl_kept[c]) / (float)nch);
   *k_out = k;
-  return nch > 0 ? (long long)cfg->cost_cluster + (long long)nch * k : 0;
+  if (nch <= 0) return 0;
+  long long w = (long long)cfg->cost_cluster + (long long)nch * k;
+  if (use_act)
+    w += (long long)kCostActive * ((long long)__ldcg(&cfg->cl_act[c]) +
+                                   (long long)max(0, nch - kActChunks) * (cs4 >> 2));
+  return w;
 }
 
 // Shared memory of the solve kernel.
@@ -1021,11 +1040,11 @@ struct SolveSmem {
 // cluster's first chunk.
 __device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, long long base,
                        long long s, int lane, int* c_out, int* j_out, int* g_out,
-                       bool use_kept) {
+                       bool use_kept, bool use_act) {
   const int c = group * 32 + lane;
   long long w = 0;
   int kk = 4;
-  if (c < cv.ncl) w = cluster_work(cfg, cv, c, &kk, use_kept);
+  if (c < cv.ncl) w = cluster_work(cfg, cv, c, &kk, use_kept, use_act);
   long long incl = w;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -1041,8 +1060,58 @@ __device__ void locate(const SolveCfg* cfg, const ClusterView& cv, int group, lo
     const int k4 = __shfl_sync(kFull, kk, src);
     const int cs4 = ((cv.cstart[cc + 1] - cv.cstart[cc]) + 3) & ~3;
     const int oh = k4 - cs4;
+    const int G = cs4 >> 2;
+    const int nch = (__ldcg(&cfg->cl_fcand[cc]) + 31) >> 5;
     int j = 0, gq = 0;
-    if (s > e) {
+    if (use_act && s > e) {
+      // chunk j costs k4 + kCostActive x (its active groups; all of them past
+      // the recorded chunks); lane j holds chunk j's mask
+      const unsigned gm = (1u << G) - 1u;
+      long long cum = 0;   // end of the chunks before this round, relative to e
+      for (int j0 = 0;; j0 += 32) {
+        const int jj = j0 + lane;
+        unsigned mj = gm;
+        if (jj < nch && jj < kActChunks) mj = __ldcg(&cfg->ch_act[(size_t)cc * kActChunks + jj]) & gm;
+        const long long kj = jj < nch ? (long long)k4 + (long long)kCostActive * __popc(mj) : 0;
+        long long in = kj;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const long long v = __shfl_up_sync(kFull, in, off);
+          if (lane >= off) in += v;
+        }
+        // the chunk whose end lies beyond s (s - e < cum + in)
+        const unsigned hit = __ballot_sync(kFull, jj < nch && s - e < cum + in);
+        if (hit) {
+          const int src2 = __ffs(hit) - 1;
+          const long long start = e + cum + __shfl_sync(kFull, in - kj, src2);
+          const unsigned m = __shfl_sync(kFull, mj, src2);
+          j = j0 + src2;
+          if (s > start) {
+            // units of the chunk: group 0 at start (with the overhead), group
+            // g at start + oh + sum over g' < g of (4 + kCostActive a_g')
+            long long u = start + oh + 4 + kCostActive * (long long)(m & 1u);
+            gq = G;
+            for (int g = 1; g < G; ++g) {
+              if (u >= s) {
+                gq = g;
+                break;
+              }
+              u += 4 + kCostActive * (long long)((m >> g) & 1u);
+            }
+            if (gq >= G) {
+              ++j;
+              gq = 0;
+            }
+          }
+          break;
+        }
+        cum += __shfl_sync(kFull, in, 31);
+        if (j0 + 32 >= nch) {   // past the last chunk (cannot happen: s < end)
+          j = nch;
+          break;
+        }
+      }
+    } else if (s > e) {
       const long long r = s - e;
       j = (int)(r / k4);
       const int rr = (int)(r - (long long)j * k4);
@@ -1113,7 +1182,7 @@ __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid,
       jj = gg = 0;
     } else {
       locate(cfg, cv, sm.bnd_group[q], sm.bnd_base[q], s, lane, &c, &jj, &gg,
-             sm.b.use_kept != 0);
+             sm.b.use_kept != 0, sm.b.use_act != 0);
     }
     if (lane == 0) {
       if (h == 0) {
@@ -1192,10 +1261,11 @@ __device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, 
 // terms are not added). The four bodies are independent, so their latencies
 // overlap.
 template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ __forceinline__ void chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, float4 xp,
-                                            const float xf[DPS], int jlo, int jhi, float rc2,
-                                            float A, float acc[7], unsigned& nnz) {
+__device__ __forceinline__ unsigned chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, float4 xp,
+                                                const float xf[DPS], int jlo, int jhi, float rc2,
+                                                float A, float acc[7], unsigned& nnz) {
   float W = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
+  unsigned active = 0u;   // bit g: source group g kept a pair (the same in every lane)
   for (int j0 = jlo; j0 < jhi; j0 += 4) {
     float ex[4], ey[4], ez[4], d2[4];
     bool keep[4];
@@ -1209,6 +1279,7 @@ __device__ __forceinline__ void chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, fl
       keep[jj] = d2[jj] <= rc2;
     }
     if (!__any_sync(kFull, keep[0] | keep[1] | keep[2] | keep[3])) continue;
+    active |= 1u << (j0 >> 2);
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int j = j0 + jj;
@@ -1268,6 +1339,7 @@ __device__ __forceinline__ void chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, fl
     acc[5] += Ey;
     acc[6] += Ez;
   }
+  return active;
 }
 
 // A warp's range of work (BlockCtx::w_*).
@@ -1386,6 +1458,16 @@ __device__ __forceinline__ void add_kept(const SolveCfg* cfg, int c, unsigned ke
   if (lane == 0 && c >= 0 && k) atomicAdd(&cfg->cl_kept[c], (int)k);
 }
 
+// Source groups of chunk j of cluster c that kept a pair, recorded by the
+// plan's first gradient pass (lane 0; the mask is warp-uniform).
+__device__ __forceinline__ void add_active(const SolveCfg* cfg, int c, int j, unsigned active,
+                                           int lane) {
+  if (lane == 0 && active && c >= 0 && j < kActChunks) {
+    atomicOr(&cfg->ch_act[(size_t)c * kActChunks + j], active);
+    atomicAdd(&cfg->cl_act[c], __popc(active));
+  }
+}
+
 // Stage cluster c for the warp from global memory (raw centred source points
 // and features, transformed by stage_cluster).
 template <bool STEP, int DP, int MODE, int DPS, int NU>
@@ -1459,7 +1541,9 @@ __device__ void pass_stream(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
         if (glo < ghi) {
           const int jlo = 4 * glo, jhi = min(cs4, 4 * ghi);
           if (j * 32 + lane < tc) cand += (unsigned)max(0, min(cs, jhi) - jlo);
-          chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, jlo, jhi, rc2, A, acc, nnz);
+          const unsigned act =
+              chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, jlo, jhi, rc2, A, acc, nnz);
+          if (collect) add_active(cfg, c, j, act, lane);
         }
       }
       if (collect) add_kept(cfg, c, nnz - nnz0, lane);
@@ -1503,7 +1587,9 @@ __device__ void pass_stream(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
       if (glo < ghi) {
         const int jlo = 4 * glo, jhi = min(cs4, 4 * ghi);
         if (have) cand += (unsigned)max(0, min(cs, jhi) - jlo);
-        chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, jlo, jhi, rc2, A, acc, nnz);
+        const unsigned act =
+            chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, jlo, jhi, rc2, A, acc, nnz);
+        if (collect) add_active(cfg, c, j, act, lane);
       }
       used += cnt;
     }
@@ -1600,6 +1686,7 @@ __device__ void fill_cache(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp
       range_groups(r, c, j, ((cs + 3) & ~3) >> 2, glo, ghi);
       const int cnt = min(32, want - 32 * lane);
       sm.cache_hdr[warp][n + lane] = (unsigned short)(cnt | (glo << 6) | (ghi << 10));
+      sm.cache_cl[warp][n + lane] = j;   // a chunk slot keeps its chunk index
     }
     n += nchk;
     __syncwarp();   // the segment arrays are reused by the next cluster
@@ -1629,9 +1716,9 @@ __device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
     if (h & kSlotCluster) {
       if (collect) {
         add_kept(cfg, cur, nnz - nnz0, lane);
-        cur = sm.cache_cl[warp][s];
         nnz0 = nnz;
       }
+      cur = sm.cache_cl[warp][s];
       __syncwarp();   // every lane is done with the previous cluster
       cs = (int)(h & 0x3f);
       stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, lane < cs, p, f);
@@ -1641,7 +1728,9 @@ __device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
       const int cnt = (int)(h & 0x3f);
       const int jlo = 4 * (int)((h >> 6) & 0xf), jhi = min(cs4, 4 * (int)((h >> 10) & 0xf));
       if (lane < cnt) cand += (unsigned)max(0, min(cs, jhi) - jlo);
-      chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, p, f, jlo, jhi, rc2, A, acc, nnz);
+      const unsigned act =
+          chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, p, f, jlo, jhi, rc2, A, acc, nnz);
+      if (collect) add_active(cfg, cur, sm.cache_cl[warp][s], act, lane);
     }
   }
   if (collect) add_kept(cfg, cur, nnz - nnz0, lane);
@@ -1765,7 +1854,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     b.need_plan = 1;
     b.done = cfg->max_iters <= 0 ? 1 : 0;
     b.converged = b.fallback = b.no_ascent = b.have_t_prev = 0;
-    b.use_kept = b.collect_kept = b.rebalance = 0;
+    b.use_kept = b.collect_kept = b.rebalance = b.use_act = 0;
     b.t = b.t_prev = 0.0;
     b.nnz_total = b.cand_total = b.nnz_grad = b.cand_grad = 0;
     b.F = b.xi_norm = 0.0;
@@ -1789,7 +1878,8 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     if (stamp) t0 = globaltimer();
     const int replan = sm.b.need_plan;
     // a new plan, or the one rebalance of a plan that is being reused: its
-    // work split redone with the kept pairs its first gradient pass counted
+    // work split redone with what its first gradient pass recorded (the source
+    // groups that kept pairs; with cost_kept > 0 the kept pairs per cluster)
     const int rebalance = !replan && sm.b.rebalance;
     if (replan || rebalance) {
       const ClusterView& cv = cfg->clusters[sm.b.level];
@@ -1798,13 +1888,18 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
           plan_cluster(cfg, sm.b, st, (int)c, lane, sm.xs[warp], sm.pf[warp], sm.fpf[warp]);
         if (!grid_sync(st, gen, &sm.flag, team.size)) break;
       }
-      if (tid == 0) sm.b.use_kept = rebalance;
+      if (tid == 0) {
+        sm.b.use_kept = rebalance && cfg->cost_kept > 0.f;
+        sm.b.use_act = rebalance && sm.b.plan_filter;
+      }
       __syncthreads();
       const int ng = (cv.ncl + 31) / 32;
       for (long long gi = gw; gi < ng; gi += NW) {
         const int c = (int)gi * 32 + lane;
         int kk;
-        long long w = c < cv.ncl ? cluster_work(cfg, cv, c, &kk, rebalance != 0) : 0;
+        long long w = c < cv.ncl ? cluster_work(cfg, cv, c, &kk, sm.b.use_kept != 0,
+                                                sm.b.use_act != 0)
+                                 : 0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(kFull, w, off);
         if (lane == 0) cfg->group_agg[gi] = w;
@@ -1814,7 +1909,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
       fill_cache<DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots);
       if (tid == 0) {
         sm.b.need_plan = 0;
-        sm.b.collect_kept = replan && cfg->cost_kept > 0.f;
+        sm.b.collect_kept = replan && (cfg->cost_kept > 0.f || sm.b.plan_filter);
         sm.b.rebalance = sm.b.collect_kept;
         if (rebalance) sm.b.rebalance = 0;
       }

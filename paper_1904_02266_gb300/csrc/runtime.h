@@ -71,6 +71,8 @@ struct Plan {
   int* cl_fcand = nullptr;
   float4* cl_box = nullptr;
   int* cl_kept = nullptr;
+  unsigned* ch_act = nullptr;
+  int* cl_act = nullptr;
   long long* group_agg = nullptr;
   int cap_iters = 0, cap_ncl = 0;
   int nblocks = 0;
