@@ -629,11 +629,23 @@ __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
 
 // The team barrier counts arrivals on one counter that is never reset during
 // a launch: generation g is complete when (g + 1) * nblk blocks have arrived.
-// Thread 0 of each block adds its arrival (no return value awaited) and polls
-// the counter; no block has to release the others.
+// Thread 0 of each block adds its arrival (a release reduction, after the
+// block's __syncthreads, so every write the block made before the barrier is
+// ordered before it) and polls the counter with acquire loads; no block has to
+// release the others.
 __device__ __forceinline__ void barrier_arrive(SolveState* st) {
-  __threadfence();   // the block's writes before the barrier, at GPU scope
-  atomicAdd(&st->bar_count, 1u);
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->bar_count) : "memory");
+}
+
+// Arrival that returns the count before it (acquire and release: the block
+// that completes a generation then reads the others' partials).
+__device__ __forceinline__ unsigned barrier_arrive_count(SolveState* st) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+               : "=r"(old)
+               : "l"(&st->bar_count)
+               : "memory");
+  return old;
 }
 
 // Wait until `target` arrivals (thread 0). A block that polls kSpinLimit times
@@ -660,7 +672,6 @@ __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) 
     const unsigned g = gen;
     barrier_arrive(st);
     const int ok = barrier_wait(st, (g + 1) * (unsigned)nblk) ? 1 : 0;
-    __threadfence();
     *s_flag = ok;
   }
   gen += 1;
@@ -741,8 +752,7 @@ __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const 
   gen += 1;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    const unsigned arrived = barrier_arrive_count(st);
     sm.last = (arrived + 1 == (g + 1) * (unsigned)nblk) ? 1 : 0;
   }
   __syncthreads();
@@ -751,8 +761,7 @@ __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const 
     if (threadIdx.x < (unsigned)nvals) st->red_sums[threadIdx.x] = sm.sums[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();
-      st_release_u32(&st->bar_rel, g + 1);
+      st_release_u32(&st->bar_rel, g + 1);   // orders the totals the block wrote before it
       sm.flag = 1;
     }
   } else if (threadIdx.x == 0) {
