@@ -324,6 +324,27 @@ def test_align_identical_clouds_stays_put(cvo):
     assert ang < 1e-6 and tr < 1e-6
 
 
+def test_step_length_with_roots_orders_of_magnitude_apart(cvo):
+    """A keyframe / frame pair of the serving workload (57k and 40k planes
+    points, seeds as the serving trace draws them) whose first step model has
+    roots five orders of magnitude apart (-3.3e-3, -5.5e-8, 2.8e-8): the first
+    maximiser must be found without fallback steps, and the solve must not
+    depend on the traversal parameters beyond the pose tolerance."""
+    X, FX = synth.stream_keyframe(623434856, 56816)
+    Z, FZ, P_gt = synth.stream_frame(623434856, 0, 39819)
+    poses = []
+    for kw in ({}, {"cell_factor": 1.0}, {"cluster_factor": 1.0}):
+        with _ctx(cvo, **kw) as ctx:
+            P, st = ctx.align(ctx.set_cloud(X, FX), ctx.set_cloud(Z, FZ))
+        assert st["status"] == 0 and st["fallback_steps"] == 0, (kw, st)
+        poses.append(P)
+    for P in poses[1:]:
+        ang, tr = oracle.pose_error(P, poses[0])
+        assert ang < POSE_TOL and tr < POSE_TOL, (ang, tr)
+    ang, tr = oracle.pose_error(poses[0], P_gt)
+    assert ang < 5e-3 and tr < 5e-3, (ang, tr)
+
+
 @pytest.mark.slow
 def test_eval_room_full_size(cvo):
     """The benchmark workload (VGA-scale room, 20k points per frame) at fixed

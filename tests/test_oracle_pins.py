@@ -284,6 +284,17 @@ def test_quartic_step_constructed_roots(oracle_mod):
         assert ok and t == pytest.approx(r1, rel=1e-9)
 
 
+def test_quartic_step_roots_orders_of_magnitude_apart(oracle_mod):
+    """G' = 4 S4 (t - r1)(t - r2)(t - r3) with S4 < 0 and roots -3.3e-3, -5.5e-8,
+    2.8e-8 (the spread met on a serving-workload pair): the model rises from
+    t = 0 and turns down at the only positive root, 2.8e-8."""
+    r1, r2, r3, S4 = -3.3e-3, -5.5e-8, 2.8e-8, -1.7e29
+    c3, c2, c1, c0 = 4 * S4, -4 * S4 * (r1 + r2 + r3), 4 * S4 * (r1 * r2 + r1 * r3 + r2 * r3), \
+        -4 * S4 * r1 * r2 * r3
+    t, ok = oracle_mod.quartic_step([1.0, c0, c1 / 2, c2 / 3, c3 / 4])
+    assert ok and t == pytest.approx(r3, rel=1e-7)
+
+
 def test_quartic_step_brute_force(oracle_mod):
     """First local maximum of the quartic on t > 0 found by scanning a fine grid."""
     rng = np.random.default_rng(21)
