@@ -274,7 +274,8 @@ typedef struct {
 typedef struct {
     int reserve_blocks;    /* block slots of the solve kernel's full occupancy that the
                               serving kernel leaves free, so that the kernels preparing new
-                              frames can run while solves do; >= 1; 8 */
+                              frames can run while solves do (a block slot is one SM);
+                              >= 1; 4 */
     int max_inflight;      /* requests admitted to the device at once, in [1, 65536]; 1024 */
     double linger_ms;      /* the serving kernel stays resident this long without work; 0.5 */
     double idle_limit_ms;  /* device-side bound on the serving kernel's wait for new requests:

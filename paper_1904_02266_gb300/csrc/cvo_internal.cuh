@@ -13,7 +13,14 @@
 
 namespace cvo {
 
-constexpr int kWarps = 8;                 // warps per block of the pair passes
+// Warps per block of the pair passes: one block of 16 warps per SM (all 64K
+// registers at 128 a thread), so that the team barriers reduce one partial
+// per SM rather than two (on GB300 that FP64 reduction runs at about 64 cycles
+// per warp instruction) at the same 16 warps per SM.
+#ifndef CVO_WARPS
+#define CVO_WARPS 16
+#endif
+constexpr int kWarps = CVO_WARPS;
 constexpr int kThreads = kWarps * 32;     // threads per block
 constexpr int kMaxLevels = 8;             // target cell lists one solve may use
 constexpr int kMaxFeatPad = 8;            // padded feature planes (3, 5 or 8)

@@ -48,7 +48,7 @@
 
 // Resident blocks per SM the solve kernel is compiled for (register budget).
 #ifndef CVO_SOLVE_MIN_BLOCKS
-#define CVO_SOLVE_MIN_BLOCKS 2
+#define CVO_SOLVE_MIN_BLOCKS 1
 #endif
 
 namespace cvo {
@@ -685,12 +685,12 @@ __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) 
 // l, l + 32, l + 64, ... in sequence (its loads issued first), then the 32 lane
 // sums are added along a fixed shuffle tree, so every FP64 instruction has all
 // its lanes busy (on GB300 an FP64 instruction costs the same with one lane or
-// 32). Warp 7 adds the two counts as integers. Results land in out[] (shared).
+// 32). The last warp adds the two counts as integers. Results land in out[] (shared).
 // Every thread of the block calls it.
 template <class Smem>
 __device__ void reduce_partials(const double* partials, int nvals, double* out, int nblk,
                                 Smem& sm) {
-  static_assert(kWarps == 8, "the counts go to warp 7");
+  static_assert(kWarps >= 8, "seven FP values and the counts need eight warps");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kMaxPer = 16;   // nblk <= 512 blocks: 16 per lane
   const int nf = nvals - 2;     // FP64 values; nf <= 7

@@ -443,7 +443,7 @@ extern "C" {
 void cvo_serve_params_default(cvo_serve_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
-  p->reserve_blocks = 8;
+  p->reserve_blocks = 4;
   p->max_inflight = 1024;
   p->linger_ms = 0.5;
   p->idle_limit_ms = 10000.0;
