@@ -78,7 +78,7 @@ def work_per_pair(D: int) -> dict:
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -98,6 +98,21 @@ def parse_args():
                     help="instead of the benchmark line, print the dense precision sweep "
                          "(100k points: FP64 reductions vs FP32 reductions vs BF16 features)")
     return ap.parse_args()
+
+
+def reduce_over_ranks(dist, ms, pairs, e2e_ms, e2e_pairs, device):
+    """Whole-job figures of a replicated run: the largest time over the ranks
+    (ms, e2e_ms) and the sum of the pairs every rank evaluated (pairs,
+    e2e_pairs). dist is None for a single process."""
+    if dist is None:
+        return ms, pairs, e2e_ms, e2e_pairs
+    import torch
+    t = torch.tensor([ms, pairs, e2e_ms, e2e_pairs], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm_ = t.clone()
+    dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm_[1].item(), mx[2].item(), sm_[3].item()
 
 
 def dist_env():
@@ -310,19 +325,9 @@ def run_cvo(args, world, rank, local):
     phases = {k: sum(r[k] for r in recs) for k in ("plan_ms", "grad_ms", "step_ms")}
     traffic = recorded_traffic("solve_kernel")
 
-    # max over ranks
-    total_ms = ms
-    if dist:
-        t = torch.tensor([ms, float(pairs), e2e_ms, float(sum(e2e_pairs))], dtype=torch.float64,
-                         device=f"cuda:{local}")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm_ = t.clone()
-        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        total_ms, pairs, e2e_ms = mx[0].item(), sm_[1].item(), mx[2].item()
-        e2e_total_pairs = sm_[3].item()
-    else:
-        e2e_total_pairs = float(sum(e2e_pairs))
+    # the slowest rank's times, every rank's pairs
+    total_ms, pairs, e2e_ms, e2e_total_pairs = reduce_over_ranks(
+        dist, ms, float(pairs), e2e_ms, float(sum(e2e_pairs)), f"cuda:{local}")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
