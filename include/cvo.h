@@ -103,7 +103,7 @@ typedef struct {
                               0 disables the rebalance; 0 */
     double team_factor;    /* batches and served requests: a pair's team gets about
                               team_factor * (its share of the estimated pair work) of the
-                              blocks, at least one; 6.0 */
+                              blocks, at least one; 4.0 */
 } cvo_params;
 
 /* One evaluation at a fixed pose (cvo_eval). */

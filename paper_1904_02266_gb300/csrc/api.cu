@@ -598,7 +598,7 @@ void cvo_params_default(cvo_params* p) {
   p->cost_chunk = 48;
   p->cost_cluster = 32;
   p->cost_kept = 0.0;
-  p->team_factor = 6.0;
+  p->team_factor = 4.0;
 }
 
 const char* cvo_strerror(int s) {
