@@ -281,6 +281,10 @@ typedef struct {
     double idle_limit_ms;  /* device-side bound on the serving kernel's wait for new requests:
                               past it the kernel exits by itself (counted in idle_exits) even if
                               the host never told it to; > 0; 10000 */
+    double team_factor;    /* a request's team gets about team_factor * (its share of the
+                              estimated work in the system) of the serving kernel's blocks, at
+                              least one; in (0, 1024]; 6.0 (cvo_params.team_factor sizes the
+                              teams of batches) */
 } cvo_serve_params;
 
 typedef struct {

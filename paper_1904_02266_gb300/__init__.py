@@ -112,7 +112,8 @@ class cvo_result(ctypes.Structure):
 
 class cvo_serve_params(ctypes.Structure):
     _fields_ = [("reserve_blocks", ctypes.c_int), ("max_inflight", ctypes.c_int),
-                ("linger_ms", ctypes.c_double), ("idle_limit_ms", ctypes.c_double)]
+                ("linger_ms", ctypes.c_double), ("idle_limit_ms", ctypes.c_double),
+                ("team_factor", ctypes.c_double)]
 
 
 class cvo_serve_stats(ctypes.Structure):

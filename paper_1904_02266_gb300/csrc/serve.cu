@@ -207,7 +207,7 @@ int publish(cvo_ctx* ctx, Serve* sv, Req* r) {
     std::atomic_thread_fence(std::memory_order_seq_cst);
   }
   const double share = r->work / std::max(r->work, sv->inflight_work + sv->pending_work + r->work);
-  const double g = std::ceil(ctx->prm.team_factor * share * sv->nblocks);
+  const double g = std::ceil(sv->prm.team_factor * share * sv->nblocks);
   const int team = (int)std::max(1.0, std::min((double)sv->nblocks, g));
   const int e = sv->n_entries;
   QueueEntry en;
@@ -371,13 +371,14 @@ int start_locked(cvo_ctx* ctx, const cvo_serve_params& prm) {
   }();
   const int per_sm = solve_blocks_per_sm(dp, kernel_mode(ctx->prm));
   if (per_sm <= 0) return fail(ctx, CVO_ERR_CUDA, "solve kernel cannot be resident");
-  // block slots left free: the frame preparation kernels (at most 32K
-  // registers and 1024 threads a block, the size of one solve block) must find
-  // room while the serving kernel holds every other slot
+  // block slots left free: the frame preparation kernels (at most 32
+  // registers x 1024 threads a block, which fit in the SM a solve block slot
+  // stands for) must find room while the serving kernel holds every other slot
   const int slots = std::min(per_sm * ctx->sms, 512);
   if (prm.reserve_blocks < 1 || prm.reserve_blocks >= slots || prm.max_inflight < 1 ||
       prm.max_inflight > 65536 || !(prm.linger_ms >= 0.0) || !std::isfinite(prm.linger_ms) ||
-      !(prm.idle_limit_ms > 0.0) || !(prm.idle_limit_ms <= 3.6e6))
+      !(prm.idle_limit_ms > 0.0) || !(prm.idle_limit_ms <= 3.6e6) || !(prm.team_factor > 0.0) ||
+      !(prm.team_factor <= 1024.0))
     return fail(ctx, CVO_ERR_INVALID_ARG, "bad serve parameters");
   sv->prm = prm;
   sv->dp = dp;
@@ -447,6 +448,7 @@ void cvo_serve_params_default(cvo_serve_params* p) {
   p->max_inflight = 1024;
   p->linger_ms = 0.5;
   p->idle_limit_ms = 10000.0;
+  p->team_factor = 6.0;
 }
 
 int cvo_serve_start(cvo_ctx* ctx, const cvo_serve_params* params) {
