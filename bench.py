@@ -292,10 +292,19 @@ def run_cvo(args, world, rank, local):
     launches = len(iters)   # one solve_kernel launch per step
     P_final = outs[-1][0]
 
-    # end to end through the public API from host buffers: upload both clouds
-    # (grids, plan and graph are rebuilt for the new target), solve, read back
+    # end to end through the public API from pinned host buffers: upload both
+    # clouds (grids, clusters and plan are rebuilt for the new pair), solve,
+    # read back the pose and statistics
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    host_in = [pinned(a) for a in (X, FX, Z, FZ)]
+    hX, hFX, hZ, hFZ = [t.numpy() for t in host_in]
+
     def e2e_step():
-        a, b = ctx.set_cloud(X, FX), ctx.set_cloud(Z, FZ)
+        a, b = ctx.set_cloud(hX, hFX), ctx.set_cloud(hZ, hFZ)
         P, st = ctx.align(a, b)
         ctx.release(a)
         ctx.release(b)
