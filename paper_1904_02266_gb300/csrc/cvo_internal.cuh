@@ -130,12 +130,10 @@ struct SolveState {
   unsigned long long nnz_total, cand_total;
   unsigned long long nnz_pass[2], cand_pass[2];
   unsigned long long nnz_eval, cand_eval;   // gradient pass of the last iteration
-  unsigned int bar_count, bar_rel;          // grid barrier: arrivals, and the last generation whose
-                                            // totals are published (zeroed before each launch)
+  unsigned int bar_count;                   // grid barrier: arrivals (zeroed before each launch)
   unsigned int join_count, leave_count;     // queued solves: blocks of the team that have started
                                             // and that are done with the entry
   unsigned long long t_begin_ns, t_end_ns;  // global timer at the start and end of the solve
-  double red_sums[10];                      // pass totals published by the barrier's last block
 };
 
 // Per-iteration record of a profiled solve (device timestamps).
@@ -164,7 +162,7 @@ struct PairResult {
 struct QueueEntry {
   const SolveCfg* cfg;
   SolveState* st;            // zeroed, with P0 set, before the entry is published
-  double* partials;          // 2 * team * kPartialStride doubles
+  double* partials;          // 2 * team * kPartialStride doubles (see launch_solve)
   PairResult* out;           // NULL: the host reads st after the launch; else written by the
                              // team's last block to finish, so that no block of the team
                              // touches the entry once out->done is set
@@ -231,7 +229,10 @@ cudaError_t build_grid(const float4* xyz, const void* feat, int n, int dp, int n
 // ---- pair_kernels.cu -------------------------------------------------------
 // The whole solve (or one evaluation, cfg->mode == kModeEval) as one
 // cooperative launch of nblocks blocks; partials holds 2 * nblocks *
-// kPartialStride doubles; records (may be NULL) one entry per iteration.
+// kPartialStride doubles, the gradient pass's block partials then the step
+// pass's, each value-major (value i of block b at i * nblocks + b, so that the
+// reduction reads each value's partials as one contiguous run); records (may
+// be NULL) one entry per iteration.
 cudaError_t launch_solve(int dp, int color_mode, int nblocks, const SolveCfg* cfg, SolveState* st,
                          double* partials, IterRecord* records, cudaStream_t s);
 // color_mode below is the kernel mode: the label product | kFeatBf16.

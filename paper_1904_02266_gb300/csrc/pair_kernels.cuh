@@ -150,6 +150,8 @@ struct BlockCtx {
   int need_plan, done, converged, fallback, no_ascent, have_t_prev;
   int use_kept, collect_kept, rebalance;   // kept-pair weighting of the work split
   int use_act;                             // the split weighs source groups by their activity
+  int team_rank, team_size;                // this block's place in its team (read after a pass
+                                           // from shared memory rather than kept in registers)
   unsigned long long nnz_total, cand_total, nnz_grad, cand_grad;
   float R[9], T[3];       // FP32 centred pose: z~' = R z' + T
   float om[3], vc[3];     // unit step direction (centred frame)
@@ -629,16 +631,11 @@ __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
 
 // The team barrier counts arrivals on one counter that is never reset during
 // a launch: generation g is complete when (g + 1) * nblk blocks have arrived.
-// Thread 0 of each block adds its arrival (a release reduction, after the
-// block's __syncthreads, so every write the block made before the barrier is
-// ordered before it) and polls the counter with acquire loads; no block has to
-// release the others.
-__device__ __forceinline__ void barrier_arrive(SolveState* st) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->bar_count) : "memory");
-}
-
-// Arrival that returns the count before it (acquire and release: the block
-// that completes a generation then reads the others' partials).
+// Thread 0 of each block adds its arrival with an acquire-release atomic after
+// the block's __syncthreads (so every write the block made before the barrier
+// is ordered before it) that returns the count before it: the block whose
+// arrival completes the generation goes on at once, the others poll the
+// counter with acquire loads. No block has to release the others.
 __device__ __forceinline__ unsigned barrier_arrive_count(SolveState* st) {
   unsigned old;
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
@@ -669,20 +666,20 @@ __device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned target) {
 __device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = gen;
-    barrier_arrive(st);
-    const int ok = barrier_wait(st, (g + 1) * (unsigned)nblk) ? 1 : 0;
-    *s_flag = ok;
+    const unsigned target = (gen + 1) * (unsigned)nblk;
+    const bool last = barrier_arrive_count(st) + 1 == target;
+    *s_flag = (last || barrier_wait(st, target)) ? 1 : 0;
   }
   gen += 1;
   __syncthreads();
   return *s_flag != 0;
 }
 
-// Fixed-order FP64 sum of the nblk block partials (nvals <= 10 values each;
-// the last two are counts, held as 64-bit integers in the doubles' bits), by
-// one block. Warp w < nvals - 2 sums value w: lane l adds the value of blocks
-// l, l + 32, l + 64, ... in sequence (its loads issued first), then the 32 lane
+// Fixed-order FP64 sum of the nblk block partials (nvals <= 10 values each,
+// value-major; the last two are counts, held as 64-bit integers in the
+// doubles' bits), by one block. Warp w < nvals - 2 sums value w, one
+// contiguous run of nblk doubles: lane l adds the value of blocks l, l + 32,
+// l + 64, ... in sequence (its loads issued first), then the 32 lane
 // sums are added along a fixed shuffle tree, so every FP64 instruction has all
 // its lanes busy (on GB300 an FP64 instruction costs the same with one lane or
 // 32). The last warp adds the two counts as integers. Results land in out[] (shared).
@@ -701,7 +698,7 @@ __device__ void reduce_partials(const double* partials, int nvals, double* out, 
 #pragma unroll
     for (int k = 0; k < kMaxPer; ++k) {
       const int blk = lane + 32 * k;
-      v[k] = blk < nblk ? __ldcg(&partials[(size_t)blk * kPartialStride + i]) : 0.0;
+      v[k] = blk < nblk ? __ldcg(&partials[(size_t)i * nblk + blk]) : 0.0;
     }
     double acc = 0.0;
     float accf = 0.f;
@@ -726,7 +723,7 @@ __device__ void reduce_partials(const double* partials, int nvals, double* out, 
       unsigned long long n = 0;
       for (int blk = lane; blk < nblk; blk += 32)
         n += (unsigned long long)__double_as_longlong(
-            __ldcg(&partials[(size_t)blk * kPartialStride + nf + c]));
+            __ldcg(&partials[(size_t)(nf + c) * nblk + blk]));
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(kFull, n, off);
       if (lane == 0) out[nf + c] = __longlong_as_double((long long)n);
@@ -735,16 +732,15 @@ __device__ void reduce_partials(const double* partials, int nvals, double* out, 
   __syncthreads();
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Barrier that also reduces the pass: the block whose arrival completes
-// generation g sums all block partials in FP64 (fixed order, all its
-// threads), publishes the totals and then raises the release flag to g + 1;
-// the others wait for the flag and read the totals (thread 0, one round
-// trip). Every thread of every block gets the totals in sums[]. Bounded like
-// grid_sync.
+// Barrier that also reduces the pass: every block adds its arrival (a release
+// reduction after the block's partials are written), waits for the
+// generation's last arrival with acquire loads, and then sums all block
+// partials itself in the same fixed FP64 order, so that no block has to
+// publish totals and release the others. A block reads the partials of
+// generation g only before it arrives at generation g + 1, and the next
+// writes to the same partial buffer (two generations later) come after that
+// arrival, so one buffer per pass kind is enough. Every thread of every block
+// gets the totals in sums[]. Bounded like grid_sync.
 template <class Smem>
 __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const double* partials,
                                  int nvals, int nblk) {
@@ -752,36 +748,14 @@ __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const 
   gen += 1;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned arrived = barrier_arrive_count(st);
-    sm.last = (arrived + 1 == (g + 1) * (unsigned)nblk) ? 1 : 0;
+    const unsigned target = (g + 1) * (unsigned)nblk;
+    const bool last = barrier_arrive_count(st) + 1 == target;
+    sm.flag = (last || barrier_wait(st, target)) ? 1 : 0;
   }
   __syncthreads();
-  if (sm.last) {
-    reduce_partials(partials, nvals, sm.sums, nblk, sm);
-    if (threadIdx.x < (unsigned)nvals) st->red_sums[threadIdx.x] = sm.sums[threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      st_release_u32(&st->bar_rel, g + 1);   // orders the totals the block wrote before it
-      sm.flag = 1;
-    }
-  } else if (threadIdx.x == 0) {
-    unsigned spins = 0;
-    int ok = 1;
-    while (ld_acquire(&st->bar_rel) < g + 1) {
-      if (++spins > kSpinLimit) {
-        atomicOr(&st->status, (int)kStatusTimeout);
-        ok = 0;
-        break;
-      }
-      __nanosleep(32);
-    }
-    if (ok) {
-      for (int i = 0; i < nvals; ++i) sm.sums[i] = __ldcg(&st->red_sums[i]);
-    }
-    sm.flag = ok;
-  }
-  __syncthreads();
-  return sm.flag != 0;
+  if (!sm.flag) return false;
+  reduce_partials(partials, nvals, sm.sums, nblk, sm);
+  return true;
 }
 
 // Start of a queued solve: wait until every block of the team has claimed its
@@ -1759,7 +1733,7 @@ __device__ __forceinline__ void pass_warp(const SolveCfg* cfg, SolveSmem<DPS, NU
 
 // One pass over the block's warps, then the block partial (fixed order).
 template <bool STEP, int DP, int MODE, int DPS, int NU>
-__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials, int rank,
+__device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* partials,
                          float* cache, int slots) {
   constexpr int NACC = STEP ? 5 : 7;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1800,7 +1774,7 @@ __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* pa
       for (int w = 0; w < kWarps; ++w) n += __float_as_uint(sm.red[w][lane]);
       s = __longlong_as_double((long long)n);   // a count: its bits, summed as an integer
     }
-    partials[(size_t)rank * kPartialStride + lane] = s;
+    partials[(size_t)lane * sm.b.team_size + sm.b.team_rank] = s;
   }
 }
 
@@ -1857,6 +1831,8 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     tc.reduce_fp32 = cfg->reduce_fp32;
     for (int i = 0; i < 16; ++i) b.P[i] = st->P0[i];
     b.k = 0;
+    b.team_rank = team.rank;
+    b.team_size = team.size;
     b.level = 0;
     b.plan_level = -1;
     b.plan_filter = 0;
@@ -1926,7 +1902,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     }
     if (stamp) t1 = globaltimer();
     // ---- gradient pass ----
-    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g, team.rank, cache, slots);
+    run_pass<false, DP, MODE, DPS, NU>(cfg, sm, part_g, cache, slots);
     if (stamp) tg1 = globaltimer();
     if (!grid_sync_reduce(st, gen, sm, part_g, 9, team.size)) break;
     if (stamp) tg2 = globaltimer();
@@ -1937,7 +1913,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     __syncthreads();
     if (stamp) t2 = globaltimer();
     // ---- step pass ----
-    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s, team.rank, cache, slots);
+    run_pass<true, DP, MODE, DPS, NU>(cfg, sm, part_s, cache, slots);
     if (stamp) ts1 = globaltimer();
     if (!grid_sync_reduce(st, gen, sm, part_s, 7, team.size)) break;
     if (stamp) ts2 = globaltimer();
