@@ -703,11 +703,17 @@ def order_study():
 
 def kernel_source_digest() -> str:
     """First 16 hex digits of the SHA-256 of the solve and queue kernels'
-    source (pair_kernels.cuh, then the dispatcher pair_kernels.cu)."""
+    code (pair_kernels.cuh, then the dispatcher pair_kernels.cu) with comments,
+    trailing blanks and empty lines removed: a comment edit leaves the compiled
+    kernels, and so a profile taken on them, unchanged."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("pair_kernels.cuh", "pair_kernels.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1904_02266_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1904_02266_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines())
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
 
 

@@ -27,9 +27,9 @@
 //              source points staged in shared memory (broadcast reads). FP32
 //              pairs, one ex2.approx per kept pair, per-lane FP32 sums,
 //              fixed-order reductions.                                 barrier
-//  tail        the block that completes the barrier reduces all block
-//              partials in FP64 in a fixed order and publishes the totals;
-//              every block runs the same FP64 tail, so no broadcast is needed.
+//  tail        every block reduces all block partials (value-major) in FP64
+//              in the same fixed order and runs the same FP64 tail, so
+//              nothing is published or broadcast.
 //  step pass   as above along the unit direction.                      barrier
 //  tail        step length, exponential-map update, next iteration.
 // The plan is reused while it still covers the cutoff: it is built with a
