@@ -701,20 +701,25 @@ def order_study():
     print(json.dumps({"order_study": out}), flush=True)
 
 
-def kernel_source_digest() -> str:
-    """First 16 hex digits of the SHA-256 of the solve and queue kernels'
-    code (pair_kernels.cuh, then the dispatcher pair_kernels.cu) with comments,
-    trailing blanks and empty lines removed: a comment edit leaves the compiled
-    kernels, and so a profile taken on them, unchanged."""
+def code_digest(sources) -> str:
+    """First 16 hex digits of the SHA-256 of C/CUDA source texts with block
+    and line comments, trailing blanks and empty lines removed."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("pair_kernels.cuh", "pair_kernels.cu"):
-        src = open(os.path.join(ROOT, "paper_1904_02266_gb300", "csrc", f)).read()
+    for src in sources:
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         lines = (re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines())
         h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_digest() -> str:
+    """code_digest of the solve and queue kernels (pair_kernels.cuh, then the
+    dispatcher pair_kernels.cu): a comment edit leaves the compiled kernels,
+    and so a profile taken on them, unchanged."""
+    return code_digest(open(os.path.join(ROOT, "paper_1904_02266_gb300", "csrc", f)).read()
+                       for f in ("pair_kernels.cuh", "pair_kernels.cu"))
 
 
 def recorded_traffic(kernel: str):
