@@ -26,7 +26,7 @@ constexpr int kMaxLevels = 8;             // target cell lists one solve may use
 constexpr int kMaxFeatPad = 8;            // padded feature planes (3, 5 or 8)
 constexpr int kMaxPoints = 1 << 22;       // largest cloud (keeps candidate counts in int32)
 constexpr int kMaxCells = 1 << 22;        // largest cell list
-constexpr int kPartialStride = 10;        // doubles per block partial
+constexpr int kPartialStride = 10;        // values per block partial (stored value-major)
 constexpr int kClusterMax = 32;           // source points per cluster
 constexpr int kMaxSeg = 64;               // cell-row segments per cluster
 constexpr int kMortonBits = 10;           // Morton quantisation per axis
