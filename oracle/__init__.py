@@ -7,7 +7,9 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 executes anything here, and nothing here imports the product library.
 
 Layout:
-  cvo_oracle.c   exhaustive all-pairs FP64 sums (F, gradient, step sums),
+  cvo_oracle.c   FP64 pair sums (F, gradient, step sums) over every pair within
+                 the cutoff, by an exhaustive loop or by a search of the
+                 27 cells of edge r_c around each source point (same bits),
                  compiled with gcc into ``_build/liboracle.so``
   __init__.py    the solver around those sums: metric scaling (Eq. metric),
                  the 4th-order Taylor step (Eq. fourth), the SE(3)
@@ -76,6 +78,10 @@ def _load():
                                                 ctypes.c_int, dp, ctypes.POINTER(_Params), dp,
                                                 ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, dp]
             lib.orc_pair_sums_per_j.restype = ctypes.c_int
+            lib.orc_pair_sums_grid.argtypes = lib.orc_pair_sums.argtypes
+            lib.orc_pair_sums_grid.restype = ctypes.c_int
+            lib.orc_pair_sums_grid_per_j.argtypes = lib.orc_pair_sums_per_j.argtypes
+            lib.orc_pair_sums_grid_per_j.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -96,7 +102,9 @@ class Params:
     schedule (0.15 -> x0.9 per iteration -> 0.02), sigma = 1, sparsification
     threshold 1e-3 (Sec. 5 / Table 1), appearance kernel with lengthscale 0.1,
     a = b = 1 in Eq. metric, at most 200 iterations, convergence thresholds
-    1e-5 / 5e-5 (Table 1)."""
+    1e-5 / 5e-5 (Table 1). ``search`` picks the exhaustive loop over all
+    pairs or the cell search (same results; the cell search needs kcut in
+    (0, 1))."""
     ell0: float = 0.15
     ell_decay: float = 0.9
     ell_min: float = 0.02
@@ -112,6 +120,7 @@ class Params:
     eps_pose: float = 1e-5
     eps_grad: float = 5e-5
     step_order: int = 4
+    search: str = "exhaustive"       # "exhaustive" or "grid": same sums, bit for bit
 
 
 def _c(a):
@@ -146,8 +155,19 @@ def _prep(X, FX, Z, FZ):
     return X, FX, Z, FZ, D
 
 
+def _search_fn(lib, prm: Params, per_j: bool):
+    if prm.search == "exhaustive":
+        return lib.orc_pair_sums_per_j if per_j else lib.orc_pair_sums
+    if prm.search == "grid":
+        if not 0.0 < prm.kcut < 1.0:
+            raise ValueError("the cell search needs kcut in (0, 1)")
+        return lib.orc_pair_sums_grid_per_j if per_j else lib.orc_pair_sums_grid
+    raise ValueError(f"unknown search {prm.search!r}")
+
+
 def pair_sums(X, FX, Z, FZ, P, ell, prm: Params, xi=None) -> dict:
-    """Exhaustive FP64 sums over every (i, j) pair that survives the cutoff.
+    """FP64 sums over every (i, j) pair that survives the cutoff (found by the
+    exhaustive loop or the cell search, ``prm.search``: the same bits).
 
     Returns F (Eq. scalar), the unscaled derivatives dF/domega and dF/dv
     (Eq. 3_gradient, left-perturbation signs), the number of kept pairs, and,
@@ -161,8 +181,9 @@ def pair_sums(X, FX, Z, FZ, P, ell, prm: Params, xi=None) -> dict:
     cp = _cparams(prm, ell)
     xi_keep = _c(xi).reshape(6) if xi is not None else None
     xip = _dptr(xi_keep) if xi_keep is not None else None
-    rc = lib.orc_pair_sums(_dptr(X), _dptr(FX), X.shape[0], _dptr(Z), _dptr(FZ), Z.shape[0], D,
-                           _dptr(P), ctypes.byref(cp), xip, _dptr(out))
+    fn = _search_fn(lib, prm, per_j=False)
+    rc = fn(_dptr(X), _dptr(FX), X.shape[0], _dptr(Z), _dptr(FZ), Z.shape[0], D,
+            _dptr(P), ctypes.byref(cp), xip, _dptr(out))
     if rc != 0:
         raise ValueError(f"oracle pair sums failed ({rc})")
     return {"F": out[0], "dF_domega": out[1:4].copy(), "dF_dv": out[4:7].copy(),
@@ -179,11 +200,12 @@ def pair_sums_per_j(X, FX, Z, FZ, P, ell, prm: Params, js, xi=None) -> np.ndarra
     out = np.zeros((js.shape[0], NOUT))
     cp = _cparams(prm, ell)
     xi_keep = _c(xi).reshape(6) if xi is not None else None
-    rc = lib.orc_pair_sums_per_j(_dptr(X), _dptr(FX), X.shape[0], _dptr(Z), _dptr(FZ), Z.shape[0],
-                                 D, _dptr(P), ctypes.byref(cp),
-                                 _dptr(xi_keep) if xi_keep is not None else None,
-                                 js.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), js.shape[0],
-                                 _dptr(out))
+    fn = _search_fn(lib, prm, per_j=True)
+    rc = fn(_dptr(X), _dptr(FX), X.shape[0], _dptr(Z), _dptr(FZ), Z.shape[0],
+            D, _dptr(P), ctypes.byref(cp),
+            _dptr(xi_keep) if xi_keep is not None else None,
+            js.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), js.shape[0],
+            _dptr(out))
     if rc != 0:
         raise ValueError(f"oracle per-j sums failed ({rc})")
     return out
