@@ -104,6 +104,14 @@ typedef struct {
     double team_factor;    /* batches and served requests: a pair's team gets about
                               team_factor * (its share of the estimated pair work) of the
                               blocks, at least one; 4.0 */
+    /* failure bounds of the device-side waits (Sec. 4's solve runs as one
+       persistent launch whose blocks wait on each other; every wait is
+       bounded so that a lost block ends the solve with CVO_ERR_TIMEOUT
+       instead of hanging the GPU): */
+    int wait_polls;        /* polls of a team barrier before a block gives up, in [1, 2^30]
+                              (each poll sleeps about 0.5 us); 4194304 (about 2 s) */
+    double join_limit_ms;  /* how long a queued pair's first block waits for the rest of its
+                              team to start, in (0, 1e7] ms; 60000 */
 } cvo_params;
 
 /* One evaluation at a fixed pose (cvo_eval). */
@@ -163,6 +171,16 @@ int cvo_release_cloud(cvo_ctx* ctx, int32_t handle);
  * *out when it returns. */
 int cvo_eval(cvo_ctx* ctx, int32_t target, int32_t source, const double P[16], double ell,
              cvo_eval_result* out);
+
+/* Set the failure bounds of the device-side waits (cvo_params.wait_polls and
+ * join_limit_ms) of the context and of every plan and batch it already holds;
+ * later solves, evaluations and batch runs use them. The paper has no
+ * counterpart: the solve of Problem 1 runs as one persistent launch whose
+ * blocks wait on each other, and these bounds turn a lost block into
+ * CVO_ERR_TIMEOUT instead of a hung GPU. Synchronous. Errors:
+ * CVO_ERR_INVALID_ARG for values outside the ranges in cvo_params,
+ * CVO_ERR_BUSY while the request loop runs. */
+int cvo_set_wait_limits(cvo_ctx* ctx, int wait_polls, double join_limit_ms);
 
 /* Full solve from P0 (Problem 1; Eqs. flow, fourth, newstep, step): gradient,
  * step sums, quartic step and exponential-map update per iteration, with the
@@ -435,9 +453,13 @@ int cvo_frontend_cloud(cvo_ctx* ctx, const float* depth, const float* hsv, int w
  * carries over between calls, but all calls on one device share the array:
  * calls whose kernels overlap on the GPU (different streams, or different
  * host threads) race and must be serialised by the caller. The first call on
- * each device looks up the array's device address; make that first call
- * before any stream capture. Sizes outside 1 <= n, m <= 2^22 return
- * CVO_ERR_INVALID_ARG; so do NULL pointers and invalid parameters. The detail
+ * each device looks up the array's device address and keeps it for the life
+ * of the process; make that first call before any stream capture. A host
+ * that destroys the device's primary context (cudaDeviceReset) invalidates
+ * that address and must reload the library before calling again. Sizes outside 1 <= n, m <= 2^22 return
+ * CVO_ERR_INVALID_ARG; so do NULL pointers and invalid parameters (a
+ * color_mode other than NONE, KERNEL or DOT; ell_color <= 0 for KERNEL or
+ * color_scale <= 0 for DOT when features are used). The detail
  * message of a failed call is returned by cvo_last_error(NULL) on the same
  * host thread. */
 int cvo_eval_gradient_static(const float* d_x, const float* d_fx, int64_t n, const float* d_z,

@@ -37,7 +37,8 @@ CVO_MAX_FEAT = 8
 
 # every entry point declared in include/cvo.h
 EXPORTS = ("cvo_params_default", "cvo_create", "cvo_destroy", "cvo_set_cloud",
-           "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile", "cvo_stream",
+           "cvo_release_cloud", "cvo_eval", "cvo_align", "cvo_align_profile",
+           "cvo_set_wait_limits", "cvo_stream",
            "cvo_batch_create", "cvo_batch_run", "cvo_batch_get_info", "cvo_batch_destroy",
            "cvo_serve_params_default", "cvo_serve_start", "cvo_submit", "cvo_poll",
            "cvo_serve_stop", "cvo_serve_get_stats", "cvo_frontend_params_default",
@@ -67,7 +68,8 @@ class cvo_params(ctypes.Structure):
                 ("feat_bf16", ctypes.c_int), ("reduce_fp32", ctypes.c_int),
                 ("cell_factor", ctypes.c_double), ("cluster_factor", ctypes.c_double),
                 ("cost_chunk", ctypes.c_int), ("cost_cluster", ctypes.c_int),
-                ("cost_kept", ctypes.c_double), ("team_factor", ctypes.c_double)]
+                ("cost_kept", ctypes.c_double), ("team_factor", ctypes.c_double),
+                ("wait_polls", ctypes.c_int), ("join_limit_ms", ctypes.c_double)]
 
 
 class cvo_eval_result(ctypes.Structure):
@@ -173,6 +175,8 @@ def load_library(path: str = LIB_PATH):
                                  ctypes.POINTER(cvo_eval_result)]
         lib.cvo_align.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, dp, dp,
                                   ctypes.POINTER(cvo_stats)]
+        lib.cvo_set_wait_limits.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        lib.cvo_set_wait_limits.restype = ctypes.c_int
         lib.cvo_align_profile.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, dp, dp,
                                           ctypes.POINTER(cvo_stats),
                                           ctypes.POINTER(cvo_iter_profile), ctypes.c_int,
@@ -320,6 +324,10 @@ def cvo_align(ctx, target: int, source: int, P0=None):
     return out, stats
 
 
+def cvo_set_wait_limits(ctx, wait_polls: int, join_limit_ms: float) -> None:
+    _check(ctx, load_library().cvo_set_wait_limits(ctx, int(wait_polls), float(join_limit_ms)))
+
+
 def cvo_align_profile(ctx, target: int, source: int, P0=None, max_records: int = 1000):
     """cvo_align with per-iteration CUDA-event timings of both pair passes."""
     _, p0 = _pose(np.eye(4) if P0 is None else P0)
@@ -357,8 +365,10 @@ def cvo_batch_create(ctx, targets, sources, ell0=None, team_sizes=None):
     return out
 
 
-def cvo_batch_run(ctx, batch, P0):
-    """P0: (n, 4, 4). Returns (poses (n, 4, 4), list of per-pair stats dicts)."""
+def cvo_batch_run(ctx, batch, P0, check: bool = True):
+    """P0: (n, 4, 4). Returns (poses (n, 4, 4), list of per-pair stats dicts);
+    with check=False a failed run returns (poses, stats, status code) instead
+    of raising, so that the per-pair statuses can be read."""
     p0 = np.ascontiguousarray(np.asarray(P0, dtype=np.float64))
     n = p0.shape[0]
     out = np.zeros((n, 4, 4))
@@ -367,6 +377,8 @@ def cvo_batch_run(ctx, batch, P0):
                                         p0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st)
     stats = [{k: getattr(st[i], k) for k, _ in cvo_stats._fields_} for i in range(n)]
+    if not check:
+        return out, stats, code
     _check(ctx, code)
     return out, stats
 
@@ -495,26 +507,66 @@ def cvo_autotune(ctx, target: int, source: int, space: cvo_tune_space | None = N
     return {k: getattr(rep, k) for k, _ in cvo_tune_report._fields_}
 
 
+def _check_static_args(x, fx, z, fz, params: cvo_params, out):
+    """Shapes, dtypes, layout and device of cvo_eval_gradient_static's tensor
+    arguments, checked before anything is launched: the kernels read exactly
+    n x 3 / m x 3 coordinates and n x feat_dim / m x feat_dim features, so a
+    wrong shape or dtype would make them read past the end of a buffer.
+    Raises ValueError."""
+    def is_tensor(t):
+        return hasattr(t, "data_ptr") and hasattr(t, "shape") and hasattr(t, "dtype")
+
+    for name, t in (("x", x), ("z", z), ("out", out)):
+        if not is_tensor(t):
+            raise ValueError(f"{name} must be a torch tensor")
+    if x.dim() != 2 or x.shape[1] != 3 or x.shape[0] < 1:
+        raise ValueError(f"x must have shape (n, 3) with n >= 1, got {tuple(x.shape)}")
+    if z.dim() != 2 or z.shape[1] != 3 or z.shape[0] < 1:
+        raise ValueError(f"z must have shape (m, 3) with m >= 1, got {tuple(z.shape)}")
+    n, m = int(x.shape[0]), int(z.shape[0])
+    D = int(params.feat_dim)
+    feats = params.color_mode != CVO_COLOR_NONE and D > 0
+    if feats:
+        for name, t, rows in (("fx", fx, n), ("fz", fz, m)):
+            if not is_tensor(t):
+                raise ValueError(f"{name} must be a torch tensor when features are used")
+            if t.dim() != 2 or tuple(t.shape) != (rows, D):
+                raise ValueError(f"{name} must have shape ({rows}, {D}), got {tuple(t.shape)}")
+    used = [("x", x), ("z", z)] + ([("fx", fx), ("fz", fz)] if feats else [])
+    for name, t in used:
+        if str(t.dtype) != "torch.float32":
+            raise ValueError(f"{name} must be float32, got {t.dtype}")
+    if str(out.dtype) != "torch.float64" or out.numel() < 8:
+        raise ValueError("out must be a float64 tensor of at least 8 elements")
+    for name, t in used + [("out", out)]:
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if not getattr(t, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA tensor")
+    devs = {t.device for _, t in used + [("out", out)]}
+    if len(devs) != 1:
+        raise ValueError(f"all tensors must be on one device, got {sorted(map(str, devs))}")
+    return n, m, feats
+
+
 def cvo_eval_gradient_static(x, fx, z, fz, params: cvo_params, P, ell: float, out,
                              stream=None) -> None:
-    """Allocation-free gradient pass on device tensors (torch CUDA float32, or
-    raw device addresses). out: a device tensor of 8 float64 (F, grad6, kept
-    pairs), written asynchronously on `stream` (default: torch's current
-    stream)."""
-    def addr(t):
-        if t is None:
-            return None
-        return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
-
-    n = int(x.shape[0])
-    m = int(z.shape[0])
+    """Allocation-free gradient pass on torch CUDA tensors: x (n, 3) and
+    z (m, 3) float32, fx (n, feat_dim) and fz (m, feat_dim) float32 (ignored,
+    may be None, when params.color_mode is NONE or feat_dim is 0), out a
+    float64 tensor of at least 8 elements (F, grad6, kept pairs), all
+    contiguous and on the current device. Written asynchronously on `stream`
+    (default: torch's current stream). Argument errors raise ValueError
+    before anything is launched."""
+    n, m, feats = _check_static_args(x, fx, z, fz, params, out)
     if stream is None:
         import torch
-        stream = torch.cuda.current_stream().cuda_stream
+        stream = torch.cuda.current_stream(x.device).cuda_stream
     _, pp = _pose(P)
-    code = load_library().cvo_eval_gradient_static(addr(x), addr(fx), n, addr(z), addr(fz), m,
-                                                   ctypes.byref(params), pp, float(ell), addr(out),
-                                                   stream if stream else None)
+    code = load_library().cvo_eval_gradient_static(
+        x.data_ptr(), fx.data_ptr() if feats else None, n, z.data_ptr(),
+        fz.data_ptr() if feats else None, m, ctypes.byref(params), pp, float(ell),
+        out.data_ptr(), stream if stream else None)
     if code != CVO_OK:
         raise CvoError(code, load_library().cvo_last_error(None).decode())
 
@@ -540,8 +592,8 @@ class Batch:
         self.n = len(targets)
         self.ptr = cvo_batch_create(ctx.ctx, targets, sources, ell0, team_sizes)
 
-    def run(self, P0):
-        return cvo_batch_run(self._ctx.ctx, self.ptr, P0)
+    def run(self, P0, check: bool = True):
+        return cvo_batch_run(self._ctx.ctx, self.ptr, P0, check)
 
     def info(self) -> dict:
         return cvo_batch_get_info(self._ctx.ctx, self.ptr)
@@ -582,6 +634,9 @@ class Context:
 
     def align(self, target: int, source: int, P0=None):
         return cvo_align(self.ctx, target, source, P0)
+
+    def set_wait_limits(self, wait_polls: int, join_limit_ms: float) -> None:
+        cvo_set_wait_limits(self.ctx, wait_polls, join_limit_ms)
 
     def align_profile(self, target: int, source: int, P0=None, max_records: int = 1000):
         return cvo_align_profile(self.ctx, target, source, P0, max_records)

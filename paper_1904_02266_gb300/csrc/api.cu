@@ -321,7 +321,7 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   double h_cur = -1.0;
   for (size_t k = 0; k < ells.size(); ++k) {
     const double rc = cutoff_radius(prm, ells[k]);
-    if (h_cur < 0.0 || (f * rc <= 0.5 * h_cur && (int)hs.size() < kMaxLevels)) {
+    if (h_cur < 0.0 || (f * rc <= CVO_LEVEL_RATIO * h_cur && (int)hs.size() < kMaxLevels)) {
       h_cur = f * rc;
       hs.push_back(h_cur);
     }
@@ -404,6 +404,8 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
   cfg.max_iters = mode == kModeEval ? 1 : prm.max_iters;
   cfg.step_order = prm.step_order;
   cfg.reduce_fp32 = prm.reduce_fp32;
+  cfg.wait_polls = (unsigned)prm.wait_polls;
+  cfg.join_limit_ns = (unsigned long long)(prm.join_limit_ms * 1e6);
   cfg.mode = mode;
   // pageable sources: the copies complete before the calls return
   CK(cudaMemcpyAsync(p->d_iters, ic.data(), sizeof(IterConst) * ic.size(), cudaMemcpyHostToDevice,
@@ -599,6 +601,8 @@ void cvo_params_default(cvo_params* p) {
   p->cost_cluster = 32;
   p->cost_kept = 0.0;
   p->team_factor = 4.0;
+  p->wait_polls = 1 << 22;
+  p->join_limit_ms = 60000.0;
 }
 
 const char* cvo_strerror(int s) {
@@ -636,7 +640,8 @@ int cvo_create(const cvo_params* params, int device, size_t hbm_budget_bytes, cv
                   p.cost_chunk <= 4096 && p.cost_cluster >= 0 && p.cost_cluster <= 65536 &&
                   p.team_factor > 0.0 && p.team_factor <= 1024.0 && p.cost_kept >= 0.0 &&
                   p.cost_kept <= 1024.0 && (p.feat_bf16 == 0 || p.feat_bf16 == 1) &&
-                  (p.reduce_fp32 == 0 || p.reduce_fp32 == 1);
+                  (p.reduce_fp32 == 0 || p.reduce_fp32 == 1) && p.wait_polls >= 1 &&
+                  p.wait_polls <= (1 << 30) && p.join_limit_ms > 0.0 && p.join_limit_ms <= 1e7;
   if (!ok) return CVO_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -822,6 +827,36 @@ int cvo_align(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],
   fill_stats(hs, stats);
   if (stats) stats->status = rc;
   return rc;
+}
+
+int cvo_set_wait_limits(cvo_ctx* ctx, int wait_polls, double join_limit_ms) {
+  if (!ctx) return CVO_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!(wait_polls >= 1 && wait_polls <= (1 << 30) && join_limit_ms > 0.0 && join_limit_ms <= 1e7))
+    return fail(ctx, CVO_ERR_INVALID_ARG, "wait_polls outside [1, 2^30] or join_limit_ms "
+                                          "outside (0, 1e7]");
+  if (serve_active(ctx))
+    return fail(ctx, CVO_ERR_BUSY, "the request loop is running (cvo_serve_stop ends it)");
+  CK(cudaSetDevice(ctx->device));
+  ctx->prm.wait_polls = wait_polls;
+  ctx->prm.join_limit_ms = join_limit_ms;
+  // every configuration already on the device: cached plans, the evaluation
+  // plan and the plans of live batches (a batch's graph reads its plans'
+  // configurations at run time)
+  std::vector<Plan*> all;
+  for (auto& kv : ctx->plans) all.push_back(kv.second);
+  if (ctx->eval_plan) all.push_back(ctx->eval_plan);
+  for (cvo_batch* b : ctx->batches)
+    for (Plan* p : b->plans) all.push_back(p);
+  for (Plan* p : all) {
+    p->h_cfg.wait_polls = (unsigned)wait_polls;
+    p->h_cfg.join_limit_ns = (unsigned long long)(join_limit_ms * 1e6);
+    CK(cudaMemcpyAsync(p->d_cfg, &p->h_cfg, sizeof(SolveCfg), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    // the copy reads h_cfg: wait before the next plan's fields change
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return CVO_OK;
 }
 
 int cvo_align_profile(cvo_ctx* ctx, int32_t target, int32_t source, const double P0[16],

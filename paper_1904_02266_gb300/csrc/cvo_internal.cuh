@@ -23,6 +23,11 @@ namespace cvo {
 constexpr int kWarps = CVO_WARPS;
 constexpr int kThreads = kWarps * 32;     // threads per block
 constexpr int kMaxLevels = 8;             // target cell lists one solve may use
+// a new cell list (and cluster size) starts when the cutoff radius has
+// shrunk to this fraction of the one the current list was built for
+#ifndef CVO_LEVEL_RATIO
+#define CVO_LEVEL_RATIO 0.5
+#endif
 constexpr int kMaxFeatPad = 8;            // padded feature planes (3, 5 or 8)
 constexpr int kMaxPoints = 1 << 22;       // largest cloud (keeps candidate counts in int32)
 constexpr int kMaxCells = 1 << 22;        // largest cell list
@@ -109,6 +114,8 @@ struct SolveCfg {
   double ell_floor, eps_pose, eps_grad;
   int max_iters, step_order, mode;
   int reduce_fp32;         // precision study: block and cross-block sums in FP32
+  unsigned wait_polls;     // team barrier: polls before a block gives up
+  unsigned long long join_limit_ns;   // queued team: longest wait for its blocks to start
 };
 
 // Mutable state of one solve (device memory). The host writes the input

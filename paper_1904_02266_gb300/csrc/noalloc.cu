@@ -58,7 +58,7 @@ na_grad_kernel(const float* __restrict__ x, const float* __restrict__ fx,
   __shared__ float4 s_x[kNaThreads];
   __shared__ float s_f[DPS][kNaThreads];
   __shared__ double s_red[kNaThreads / 32][7];
-  __shared__ unsigned s_cnt[kNaThreads / 32];
+  __shared__ unsigned long long s_cnt[kNaThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double x0[3] = {x[0], x[1], x[2]};
   const double z0[3] = {z[0], z[1], z[2]};
@@ -72,7 +72,8 @@ na_grad_kernel(const float* __restrict__ x, const float* __restrict__ fx,
     T[r] = (float)tr;   // z~' = R (z - z0) + T', T' = R z0 + T - x0
   }
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  unsigned cnt = 0;
+  // kept pairs: up to n x m = 2^44 over a block, so 64-bit
+  unsigned long long cnt = 0;
   for (int j0 = blockIdx.x * kNaThreads; j0 < a.m; j0 += gridDim.x * kNaThreads) {
     const int j = j0 + tid;
     const bool zv = j < a.m;
@@ -151,7 +152,7 @@ na_grad_kernel(const float* __restrict__ x, const float* __restrict__ fx,
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) s_red[warp][k] = v;
   }
-  unsigned c = cnt;
+  unsigned long long c = cnt;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
   if (lane == 0) s_cnt[warp] = c;
@@ -210,6 +211,15 @@ extern "C" int cvo_eval_gradient_static(const float* d_x, const float* d_fx, int
   if (!(ell > 0.0) || !std::isfinite(ell) || !(p.kcut > 0.0 && p.kcut < 1.0) || !(p.sigma > 0.0) ||
       !(p.a2 > 0.0) || !(p.b2 > 0.0) || p.feat_dim < 0 || p.feat_dim > CVO_MAX_FEAT)
     return na_fail(CVO_ERR_INVALID_ARG, "invalid parameters");
+  if (p.color_mode != CVO_COLOR_NONE && p.color_mode != CVO_COLOR_KERNEL &&
+      p.color_mode != CVO_COLOR_DOT)
+    return na_fail(CVO_ERR_INVALID_ARG, "color_mode must be CVO_COLOR_NONE, _KERNEL or _DOT");
+  if (p.color_mode == CVO_COLOR_KERNEL && p.feat_dim > 0 &&
+      !(p.ell_color > 0.0 && std::isfinite(p.ell_color)))
+    return na_fail(CVO_ERR_INVALID_ARG, "ell_color must be finite and > 0");
+  if (p.color_mode == CVO_COLOR_DOT && p.feat_dim > 0 &&
+      !(p.color_scale > 0.0 && std::isfinite(p.color_scale)))
+    return na_fail(CVO_ERR_INVALID_ARG, "color_scale must be finite and > 0");
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(P[i])) return na_fail(CVO_ERR_INVALID_ARG, "pose has a non-finite entry");
   int mode = p.color_mode;
@@ -249,8 +259,6 @@ extern "C" int cvo_eval_gradient_static(const float* d_x, const float* d_fx, int
   a.n = (int)n;
   a.m = (int)m;
   a.D = D;
-  if (mode == CVO_COLOR_KERNEL && !(p.ell_color > 0.0))
-    return na_fail(CVO_ERR_INVALID_ARG, "ell_color must be > 0");
   const int nblocks = (int)std::min<int64_t>((m + kNaThreads - 1) / kNaThreads, kNaMaxBlocks);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;

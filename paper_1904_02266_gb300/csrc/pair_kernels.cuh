@@ -57,9 +57,6 @@ namespace {
 
 constexpr float kFar = 1.0e18f;   // coordinate of padding points: never within any cutoff
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned kSpinLimit = 1u << 22;   // barrier polls before giving up (~2 s)
-// a queued team waits for its last block to come free for at most this long
-constexpr unsigned long long kJoinLimitNs = 60ull * 1000 * 1000 * 1000;
 constexpr double kSkin = 0.10;              // plan radius margin (fraction of the cutoff)
 constexpr double kLoose = 1.25;             // replan when the plan radius exceeds this factor
 constexpr int kFilterMax = 1024;            // candidates of a cluster the plan filters at most
@@ -135,6 +132,8 @@ struct TailConst {
   double ell_floor, eps_pose, eps_grad, src_radius;
   int mode, step_order, max_iters;
   int reduce_fp32;   // precision study: block and cross-block sums in FP32
+  unsigned wait_polls;                 // barrier polls before a block gives up
+  unsigned long long join_limit_ns;    // longest wait of a queued team's join
 };
 
 struct BlockCtx {
@@ -645,14 +644,14 @@ __device__ __forceinline__ unsigned barrier_arrive_count(SolveState* st) {
   return old;
 }
 
-// Wait until `target` arrivals (thread 0). A block that polls kSpinLimit times
+// Wait until `target` arrivals (thread 0). A block that polls `limit` times
 // raises kStatusTimeout and returns false; its team then leaves the solve loop
 // when the other blocks' own waits run out at the next barrier, which the
 // timed-out block never reaches (an error path, bounded).
-__device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned target) {
+__device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned target, unsigned limit) {
   unsigned spins = 0;
   while (ld_acquire(&st->bar_count) < target) {
-    if (++spins > kSpinLimit) {
+    if (++spins > limit) {
       atomicOr(&st->status, (int)kStatusTimeout);
       return false;
     }
@@ -663,12 +662,12 @@ __device__ __forceinline__ bool barrier_wait(SolveState* st, unsigned target) {
 
 // Bounded barrier of the team's nblk blocks. Every block calls it the same
 // number of times; all blocks are resident (cooperative launch).
-__device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk) {
+__device__ bool grid_sync(SolveState* st, unsigned& gen, int* s_flag, int nblk, unsigned limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned target = (gen + 1) * (unsigned)nblk;
     const bool last = barrier_arrive_count(st) + 1 == target;
-    *s_flag = (last || barrier_wait(st, target)) ? 1 : 0;
+    *s_flag = (last || barrier_wait(st, target, limit)) ? 1 : 0;
   }
   gen += 1;
   __syncthreads();
@@ -750,7 +749,7 @@ __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const 
   if (threadIdx.x == 0) {
     const unsigned target = (g + 1) * (unsigned)nblk;
     const bool last = barrier_arrive_count(st) + 1 == target;
-    sm.flag = (last || barrier_wait(st, target)) ? 1 : 0;
+    sm.flag = (last || barrier_wait(st, target, sm.b.tc.wait_polls)) ? 1 : 0;
   }
   __syncthreads();
   if (!sm.flag) return false;
@@ -761,8 +760,8 @@ __device__ bool grid_sync_reduce(SolveState* st, unsigned& gen, Smem& sm, const 
 // Start of a queued solve: wait until every block of the team has claimed its
 // slot. Blocks of a team come free at different times (each finishes the pair
 // it held), so this wait can last as long as one pair's solve; it is bounded
-// by kJoinLimitNs of the global timer, after which the pair fails with
-// kStatusTimeout.
+// by join_limit_ns of the global timer (SolveCfg), after which the pair fails
+// with kStatusTimeout.
 template <class Smem>
 __device__ bool team_join(SolveState* st, int team_size, Smem& sm) {
   __syncthreads();
@@ -773,7 +772,7 @@ __device__ bool team_join(SolveState* st, int team_size, Smem& sm) {
     const unsigned long long t_start = globaltimer();
     unsigned polls = 0;
     while (ld_acquire(&st->join_count) < (unsigned)team_size) {
-      if ((++polls & 255u) == 0 && globaltimer() - t_start > kJoinLimitNs) {
+      if ((++polls & 255u) == 0 && globaltimer() - t_start > sm.b.tc.join_limit_ns) {
         ok = 0;
         atomicOr(&st->status, (int)kStatusTimeout);
         break;
@@ -1829,6 +1828,8 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     tc.step_order = cfg->step_order;
     tc.max_iters = cfg->max_iters;
     tc.reduce_fp32 = cfg->reduce_fp32;
+    tc.wait_polls = cfg->wait_polls;
+    tc.join_limit_ns = cfg->join_limit_ns;
     for (int i = 0; i < 16; ++i) b.P[i] = st->P0[i];
     b.k = 0;
     b.team_rank = team.rank;
@@ -1871,7 +1872,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
       if (replan) {
         for (long long c = gw; c < cv.ncl; c += NW)
           plan_cluster(cfg, sm.b, st, (int)c, lane, sm.xs[warp], sm.pf[warp], sm.fpf[warp]);
-        if (!grid_sync(st, gen, &sm.flag, team.size)) break;
+        if (!grid_sync(st, gen, &sm.flag, team.size, sm.b.tc.wait_polls)) break;
       }
       if (tid == 0) {
         sm.b.use_kept = rebalance && cfg->cost_kept > 0.f;
@@ -1889,7 +1890,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
         for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(kFull, w, off);
         if (lane == 0) cfg->group_agg[gi] = w;
       }
-      if (!grid_sync(st, gen, &sm.flag, team.size)) break;
+      if (!grid_sync(st, gen, &sm.flag, team.size, sm.b.tc.wait_polls)) break;
       split_work<DPS, NU>(cfg, sm, tid, team);
       fill_cache<DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots);
       if (tid == 0) {

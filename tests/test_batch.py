@@ -133,3 +133,30 @@ def test_batch_errors_and_busy_clouds(cvo, uneven):
         assert e.value.code == cvo.CVO_ERR_INVALID_ARG
         b.close()
         ctx.release(s)   # free again once the batch is gone
+
+
+def test_batch_matches_oracle_at_batch_workload_sizes(cvo):
+    """Pairs of the batch workload's sizes (10k-40k points per cloud), twelve
+    in one launch so that teams of different sizes share the GPU; three of
+    them (the largest, a mid-sized one and one with a 10k-point source) are
+    held to the oracle's own solve (cell search, the same bits as the
+    exhaustive loop): pose within 1e-4 rad / 1e-4 m, iterations within 3."""
+    pairs = synth.batch_pairs(n_pairs=12, seed=synth.seed_for(3, 3), n_range=(10000, 40000))
+    with cvo.Context(device=0) as ctx:
+        hs = [(ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])) for d in pairs]
+        with ctx.batch([t for t, _ in hs], [s for _, s in hs],
+                       ell0=[d["ell0"] for d in pairs]) as b:
+            teams = b.info()["teams"]
+            P, stats = b.run(np.stack([np.eye(4)] * len(pairs)))
+        sizes = [len(d["X"]) * len(d["Z"]) for d in pairs]
+        pick = [int(np.argmax(sizes)), 0, 2]
+        assert len(set(teams[pick])) > 1 or teams.max() > 1
+        for i in pick:
+            d = pairs[i]
+            prm = _oracle_params(ctx.params, d["ell0"])
+            prm.search = "grid"
+            res = oracle.align(d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4), prm)
+            ang, tr = oracle.pose_error(P[i], res["P"])
+            assert stats[i]["status"] == 0
+            assert ang < POSE_TOL and tr < POSE_TOL, (i, teams[i], ang, tr)
+            assert abs(stats[i]["iters"] - res["iters"]) <= 3, (i, stats[i]["iters"], res["iters"])
