@@ -5,21 +5,30 @@ Workload: one VGA-scale frame pair. A procedural room is ray-cast to 640x480
 depth + colour, the high-gradient pixels are kept and subsampled to 20,000
 points per frame, and the second frame follows a 3 deg / 3 cm camera motion.
 One step is one full solve (cvo_align) from the identity: every iteration's
-gradient pass, step pass, FP64 step and exponential-map update, on the device.
+gradient pass, step pass, FP64 step and exponential-map update, on the device,
+with the clouds (and their cell lists and clusters) resident.
 
 Metric: pair evaluations per second (Gpairs/s). A pair evaluation is one kept
 (in-cutoff) (i, j) pair in one gradient or step pass. frame_pairs_per_s is
-reported beside it.
+reported beside it. The roofline divides the kept pairs' algorithmic FP32
+instructions per second by the FP32 issue peak measured on the device
+(peaks.cu), for the whole solve and pass by pass.
 
-Two more measurements ride on the same line at N = 1 (each against plain
-one-pair-at-a-time solves of the same work, with the largest pose difference
-between the two):
+More measurements ride on the same line at N = 1:
   batch    256 uneven pairs (planes, 2k-40k points, own ell0 each) solved by
-           one persistent launch replayed from a CUDA graph (cvo_batch_run);
-  serving  an open-loop trace of 64 camera streams at 30 Hz (Poisson arrivals,
-           frames of 5k-60k points, a new keyframe every 10 frames) for
-           --serve-seconds of arrivals, through cvo_submit / cvo_poll, with
-           p50 / p99 latency from arrival to result.
+           one persistent launch replayed from a CUDA graph (cvo_batch_run),
+           with FP32 and with BF16 appearance features, against plain
+           one-pair-at-a-time solves;
+  dense    one 100,000-point room pair, its solve time, per-pass roofline and
+           pose against the oracle's stored solve;
+  serving  open-loop traces of 64 camera streams (Poisson arrivals, frames of
+           5k-60k points, a new keyframe every 10 frames) through cvo_submit /
+           cvo_poll against plain solves of the same trace: the overload
+           point (30 Hz per stream), then 0.5, 0.8 and 1.0 of the measured
+           served capacity and a long run at 0.8, with p50 / p99 latency from
+           arrival to result;
+  cpu_baseline  one whole solve of the room pair by the FP64 oracle (cell
+           search) on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cvo|reference]
 
@@ -27,9 +36,9 @@ For N > 1 launch under torch.distributed.run. Every rank solves its own copy
 of the workload (the solve does not shard; replicas only), and the value is
 all ranks' pairs divided by the slowest rank's time.
 
---impl reference times the FP64 CPU oracle on this machine's host cores on a
-bounded sample of the same workload: each step is one iteration (gradient
-pass + step pass) of the solve.
+--impl reference times the FP64 CPU oracle on this machine's host cores on the
+same workload: each step is one iteration (gradient pass + step pass + step)
+of consecutive whole solves of the room pair.
 """
 from __future__ import annotations
 
@@ -57,12 +66,10 @@ WORKLOAD = ("room VGA pair: 640x480 ray-cast room (6x5x3 m box + 20 cuboids), "
             "80th-percentile gradient pixels subsampled to 20000 points/frame, 3 deg / 3 cm "
             "motion, 5-D features, ell 0.15 x0.9 -> 0.02, kcut 1e-3, <= 200 iterations")
 
-# FP32/MUFU roofline of the pair passes. Peaks from the unit counts and the
-# maximum SM clock: 152 SMs x 128 FP32 lanes (one FP32 instruction per lane
-# per clock) and 16 MUFU (ex2) lanes per SM, at 2070 MHz.
-SMS, FP32_LANES, MUFU_LANES, SM_MAX_MHZ = 152, 128, 16, 2070.0
-PEAK_FP32_TINST = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12   # 40.3 T FP32 instructions/s
-PEAK_MUFU_TINST = SMS * MUFU_LANES * SM_MAX_MHZ * 1e6 / 1e12
+# FP32/MUFU roofline of the pair passes. The denominators are measured on the
+# device by peaks.cu (measure_peaks); the unit-count figure (SMs x 128 FP32
+# lanes x the maximum SM clock) is reported beside them as context.
+FP32_LANES, MUFU_LANES = 128, 16
 
 
 def work_per_pair(D: int) -> dict:
@@ -75,6 +82,65 @@ def work_per_pair(D: int) -> dict:
     return {"grad": 12 + 2 * D, "step": 42 + 2 * D, "mufu": 1}
 
 
+def measure_peaks(local: int) -> dict:
+    """FP32 FFMA and MUFU ex2 issue peaks of this GPU, measured by peaks.cu
+    (every SM's pipe kept full, best of five timed launches after a warm-up,
+    CUDA events), with the SM clock the kernel itself measured (clock64
+    against the global timer) and the device's SM count."""
+    import ctypes
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__.build_peaks())
+    fn = lib.peaks_measure
+    dbl = ctypes.POINTER(ctypes.c_double)
+    fn.argtypes = [ctypes.c_int] * 5 + [dbl, dbl, dbl, ctypes.POINTER(ctypes.c_int)]
+    fn.restype = ctypes.c_int
+    out = {}
+    for name, kind, iters in (("fp32", 0, 4000), ("mufu_ex2", 1, 500)):
+        ips, mhz, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        rc = fn(local, kind, 4, iters, 5, ctypes.byref(ips), ctypes.byref(mhz), ctypes.byref(ms),
+                ctypes.byref(sms))
+        if rc != 0:
+            raise RuntimeError(f"peaks_measure({name}) failed with CUDA error {rc}")
+        out[name] = {"tinst_per_s": ips.value / 1e12, "sm_mhz": mhz.value, "ms": ms.value,
+                     "per_sm_per_clock": ips.value / (sms.value * mhz.value * 1e6)}
+        out["sms"] = sms.value
+    return out
+
+
+def pass_roofline(recs, wpp, peak_fp32):
+    """Roofline fractions of the two pair passes from the per-iteration device
+    timestamps of a profiled solve (block 0): a pass's time runs from its start
+    to the moment block 0 leaves the team barrier that ends it (every block's
+    pass plus the cross-block FP64 reduction); the iteration's time adds the
+    plan and the two FP64 tails. Split into the iterations at the lengthscale
+    floor (the plan reused) and the decaying ones (a new plan each)."""
+    if not recs:
+        return None
+    floor = min(r["ell"] for r in recs)
+
+    def frac(inst, ms):
+        return inst / (ms * 1e-3) / 1e12 / peak_fp32 if ms > 0 else None
+
+    def part(sel):
+        gp = sum(r["grad_pairs"] for r in sel)
+        sp = sum(r["step_pairs"] for r in sel)
+        g_ms = sum(r["grad_sync_ms"] for r in sel)
+        s_ms = sum(r["step_sync_ms"] for r in sel)
+        it_ms = sum(r["plan_ms"] + r["grad_ms"] + r["step_ms"] for r in sel)
+        gi, si = gp * wpp["grad"], sp * wpp["step"]
+        return {"iters": len(sel),
+                "gradient": {"pairs": gp, "pass_ms": g_ms, "frac": frac(gi, g_ms)},
+                "step": {"pairs": sp, "pass_ms": s_ms, "frac": frac(si, s_ms)},
+                "both_passes": {"pass_ms": g_ms + s_ms, "frac": frac(gi + si, g_ms + s_ms)},
+                "iteration": {"ms": it_ms, "frac": frac(gi + si, it_ms),
+                              "plan_ms": sum(r["plan_ms"] for r in sel),
+                              "tails_ms": it_ms - g_ms - s_ms - sum(r["plan_ms"] for r in sel)}}
+
+    return {"all": part(recs), "floor": part([r for r in recs if r["ell"] == floor]),
+            "decaying": part([r for r in recs if r["ell"] != floor]),
+            "timing": "device timestamps of block 0 in one profiled solve (cvo_align_profile)"}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -83,7 +149,13 @@ def parse_args():
     ap.add_argument("--impl", default="cvo", choices=["cvo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=256)
-    ap.add_argument("--serve-seconds", type=float, default=0.5)
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="arrivals of the overload point (64 streams at 30 Hz)")
+    ap.add_argument("--serve-load-seconds", type=float, default=3.0,
+                    help="arrivals of each load point at 0.5, 0.8 and 1.0 of served capacity")
+    ap.add_argument("--serve-long-seconds", type=float, default=20.0,
+                    help="arrivals of the long load point (0.8 of served capacity); 0: skip")
+    ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--tuned", default="",
@@ -179,37 +251,51 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline_sample(d, n_iters: int, prm=None):
-    """The oracle as it stands, timed on the host cores: the first n_iters
-    iterations of the same solve. Returns (Gpairs/s, cores, seconds, pairs)."""
+def cpu_baseline_solve(d) -> dict:
+    """The oracle as it stands, timed on the host cores: one whole solve of
+    the same pair from the identity (every iteration to the stop test), FP64,
+    with its cell search (the exhaustive loop's bits at a fraction of its
+    pair tests)."""
     import oracle
-    prm = prm or oracle.Params(max_iters=n_iters)
+    prm = oracle.Params(search="grid")
     t0 = time.perf_counter()
     r = oracle.align(d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4), prm)
     dt = time.perf_counter() - t0
-    return r["pair_evals"] / dt / 1e9, oracle.num_threads(), dt, r["pair_evals"]
+    return {"value": r["pair_evals"] / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "frame_pairs_per_s": 1.0 / dt, "seconds": dt,
+            "sample": f"whole solve, grid mode: one full FP64 solve of the same room pair "
+                      f"({r['iters']} iterations, {r['pair_evals']} kept pair evaluations, "
+                      f"cell search over the 27 cells of edge r_c per source point)"}
 
 
 def run_reference(args, world, rank):
-    """FP64 CPU oracle arm: each step is one iteration of the solve."""
+    """FP64 CPU oracle arm: the same room-pair solve (cell search, all host
+    cores), one iteration (gradient pass + step pass + step) per step: step k
+    is iteration k of a solve that starts again from the identity after its
+    stop test fires, so K timed steps are K consecutive iterations of whole
+    solves (warm-up steps included in the sequence)."""
     if rank != 0:
         return
     import oracle
     d = synth.room_pair(N_POINTS, seed=synth.seed_for(2))
-    prm = oracle.Params()
-    ells = oracle.ell_schedule(prm, 8)
-    P = np.eye(4)
-    times, pairs = [], 0
+    prm = oracle.Params(search="grid")
+
+    def solves():
+        while True:
+            yield from oracle.iterate(d["X"], d["FX"], d["Z"], d["FZ"], np.eye(4), prm)
+
+    it = solves()
+    times, pairs, iters, solve_len = [], 0, 0, None
     for k in range(args.warmup + args.steps):
-        ell = ells[k % len(ells)]
         t0 = time.perf_counter()
-        s = oracle.pair_sums(d["X"], d["FX"], d["Z"], d["FZ"], P, ell, prm)
-        xi = oracle.gradient(s, prm)
-        s2 = oracle.pair_sums(d["X"], d["FX"], d["Z"], d["FZ"], P, ell, prm, xi=xi)
+        r = next(it)
         dt = time.perf_counter() - t0
+        if r["stop"] and solve_len is None:
+            solve_len = r["k"] + 1
         if k >= args.warmup:
             times.append(dt)
-            pairs += s["nnz"] + s2["nnz"]
+            pairs += r["pairs"]
+            iters += 1
     total = sum(times)
     value = pairs / total / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -217,12 +303,17 @@ def run_reference(args, world, rank):
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "l2": "inputs re-read from host memory"},
+            "config": {"workload": WORKLOAD, "l2": "host memory (CPU)"},
+            # whole solves per second at the measured rate (once a solve has ended
+            # within the run, so that its iteration count is known)
+            "frame_pairs_per_s": iters / solve_len / total if solve_len else None,
+            "iters_per_solve": solve_len,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
-                             "sample": "one solve iteration (gradient + step pass, exhaustive "
-                                       "all-pairs FP64) per step, ell cycling over the first 8 "
-                                       "schedule values, identity pose, full 20000x20000 pair"},
+                             "sample": f"{args.steps} consecutive iterations (gradient + step "
+                                       f"pass + step) of whole FP64 solves of the full "
+                                       f"{N_POINTS}x{N_POINTS} room pair, cell search, after "
+                                       f"{args.warmup} warm-up iterations"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -278,6 +369,7 @@ def run_cvo(args, world, rank, local):
             outs.append(out)
         return tot_ms, outs
 
+    peaks = measure_peaks(local)
     for _ in range(max(3, args.warmup)):
         ctx.align(ht, hs)
     if dist:
@@ -319,9 +411,12 @@ def run_cvo(args, world, rank, local):
 
     # roofline of the solve kernel (the only kernel of a timed step): algorithmic
     # FP32 instructions of the kept pairs of one solve over the CUDA-event time
-    # per solve; the per-phase split comes from the kernel's own timestamps
+    # per solve, against the measured FP32 issue peak; the per-pass split comes
+    # from the kernel's own timestamps
     _, pst, recs = ctx.align_profile(ht, hs)
     wpp = work_per_pair(D)
+    peak_fp32 = peaks["fp32"]["tinst_per_s"]
+    peak_mufu = peaks["mufu_ex2"]["tinst_per_s"]
     grad_pairs = sum(r["grad_pairs"] for r in recs)
     step_pairs = sum(r["step_pairs"] for r in recs)
     cand = sum(r["grad_candidates"] for r in recs)
@@ -329,10 +424,12 @@ def run_cvo(args, world, rank, local):
     solve_s = ms / args.steps * 1e-3
     achieved = inst_per_solve / solve_s / 1e12
     # roofline time: the larger of the FP32 and MUFU times of the kept pairs
-    t_roof = max(inst_per_solve / (PEAK_FP32_TINST * 1e12),
-                 (grad_pairs + step_pairs) * wpp["mufu"] / (PEAK_MUFU_TINST * 1e12))
+    t_roof = max(inst_per_solve / (peak_fp32 * 1e12),
+                 (grad_pairs + step_pairs) * wpp["mufu"] / (peak_mufu * 1e12))
     phases = {k: sum(r[k] for r in recs) for k in ("plan_ms", "grad_ms", "step_ms")}
     traffic = recorded_traffic("solve_kernel")
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    derived = peaks["sms"] * FP32_LANES * sm_max * 1e6 / 1e12
 
     # the slowest rank's times, every rank's pairs
     total_ms, pairs, e2e_ms, e2e_total_pairs = reduce_over_ranks(
@@ -348,6 +445,10 @@ def run_cvo(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points_per_frame": N_POINTS, "feat_dim": D,
                    "l2": "flushed between steps (256 MB write)",
+                   "resident": "value times cvo_align on resident clouds: the target's cell "
+                               "lists (a1) and the source clusters are built once per cloud and "
+                               "cached, so they are outside its timed region; e2e uploads both "
+                               "clouds every step and so rebuilds them",
                    "parallelism": "replicas" if world > 1 else "single",
                    "tuning": "fixed by --tuned" if fixed else "autotuned before timing",
                    "autotuned": {k: tune[k] for k in ("cell_factor", "cluster_factor",
@@ -362,29 +463,34 @@ def run_cvo(args, world, rank, local):
                 "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "solve_kernel", "achieved": achieved,
-                     "peak": PEAK_FP32_TINST, "unit": "T FP32 inst/s",
-                     "frac": achieved / PEAK_FP32_TINST, "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)",
+                     "peak": peak_fp32, "unit": "T FP32 inst/s",
+                     "frac": achieved / peak_fp32, "traffic": traffic,
+                     "peak_source": "measured: FP32 FFMA issue rate of peaks.cu on this GPU "
+                                    "(of measured)",
+                     "peak_measured": peaks,
+                     "peak_derived": {"tinst_per_s": derived,
+                                      "how": f"{peaks['sms']} SMs x {FP32_LANES} FP32 lanes x "
+                                             f"{sm_max:.0f} MHz (max SM clock)"},
                      "work": f"{wpp['grad']} FP32 inst per kept gradient-pass pair, "
                              f"{wpp['step']} per kept step-pass pair, 1 MUFU ex2 each",
                      "inst_per_launch": inst_per_solve,
                      "roofline_ms": t_roof * 1e3,
-                     "frac_at_sampled_clock": (t_roof / solve_s) * SM_MAX_MHZ
-                                              / max(1.0, (clocks or {}).get("sm_mhz") or SM_MAX_MHZ),
-                     "phase_ms_per_solve": phases},
+                     "frac_mufu": (grad_pairs + step_pairs) * wpp["mufu"] / solve_s / 1e12
+                                  / peak_mufu,
+                     "phase_ms_per_solve": phases,
+                     "per_pass": pass_roofline(recs, wpp, peak_fp32)},
         "clocks": clocks,
     }
     ctx.close()
     if world == 1 and not args.no_batch:
-        line["batch"] = bench_batch(cvo, torch, local, args.batch_pairs, flush)
+        line["batch"] = bench_batch(cvo, torch, local, args.batch_pairs, flush, peak_fp32)
+    if world == 1 and not args.no_dense:
+        line["dense"] = bench_dense(cvo, torch, local, flush, peak_fp32)
     if world == 1 and not args.no_serve:
-        line["serving"] = bench_serving(cvo, args.serve_seconds)
+        line["serving"] = bench_serving(cvo, args.serve_seconds, args.serve_load_seconds,
+                                        args.serve_long_seconds)
     if not args.no_cpu_baseline and world == 1:
-        v, cores, dt, cp = cpu_baseline_sample(d, 6)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"first 6 iterations of the same solve, exhaustive "
-                                          f"FP64 all-pairs oracle ({cp} kept pair evals, "
-                                          f"{dt:.1f} s)"}
+        line["cpu_baseline"] = cpu_baseline_solve(d)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -394,12 +500,12 @@ def _events(torch, stream):
     return (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
 
-def bench_batch(cvo, torch, local, n_pairs, flush):
-    """Uneven pairs in one persistent launch vs one plain solve per pair."""
-    pairs = synth.batch_pairs(n_pairs=n_pairs, seed=synth.seed_for(3))
+def _batch_runs(cvo, torch, local, pairs, flush, **ctx_kw):
+    """Build the batch of `pairs` in one context and time three graph replays
+    (L2 flushed before each); returns (best ms, poses, stats, info)."""
     ell0 = [d["ell0"] for d in pairs]
-    P0 = np.stack([np.eye(4)] * n_pairs)
-    with cvo.Context(device=local) as ctx:
+    P0 = np.stack([np.eye(4)] * len(pairs))
+    with cvo.Context(device=local, **ctx_kw) as ctx:
         hs = [(ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])) for d in pairs]
         stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
         with ctx.batch([t for t, _ in hs], [s for _, s in hs], ell0=ell0) as b:
@@ -416,8 +522,21 @@ def bench_batch(cvo, torch, local, n_pairs, flush):
                     e1.record(stream)
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
-    t_batch = min(ms)
+    return min(ms), P, st, info
+
+
+def bench_batch(cvo, torch, local, n_pairs, flush, peak_fp32):
+    """Uneven pairs in one persistent launch vs one plain solve per pair, and
+    the same batch with BF16 appearance features (config 3's two arms)."""
+    pairs = synth.batch_pairs(n_pairs=n_pairs, seed=synth.seed_for(3))
+    ell0 = [d["ell0"] for d in pairs]
+    t_batch, P, st, info = _batch_runs(cvo, torch, local, pairs, flush)
     pe = sum(x["pair_evals"] for x in st)
+    # both passes of an iteration keep the same pairs, so a pair evaluation
+    # costs (grad + step) / 2 algorithmic FP32 instructions on average
+    w_avg = 0.5 * (work_per_pair(5)["grad"] + work_per_pair(5)["step"])
+    t_bf, P_bf, st_bf, _ = _batch_runs(cvo, torch, local, pairs, flush, feat_bf16=1)
+    pe_bf = sum(x["pair_evals"] for x in st_bf)
     plain_ms, plain_pe, worst = 0.0, 0, 0.0
     for i, d in enumerate(pairs):
         with cvo.Context(device=local, ell0=ell0[i]) as c2:
@@ -436,35 +555,120 @@ def bench_batch(cvo, torch, local, n_pairs, flush):
                         f"ell0 ~ U[0.12, 0.18]",
             "ms_per_batch": t_batch, "frame_pairs_per_s": n_pairs / (t_batch * 1e-3),
             "gpairs_per_s": pe / (t_batch * 1e-3) / 1e9,
-            # both passes of an iteration keep the same pairs, so a pair evaluation
-            # costs (grad + step) / 2 algorithmic FP32 instructions on average
-            "roofline_frac": pe / (t_batch * 1e-3) * 0.5 * (work_per_pair(5)["grad"]
-                                                             + work_per_pair(5)["step"])
-                             / (PEAK_FP32_TINST * 1e12),
+            "roofline_frac": pe / (t_batch * 1e-3) * w_avg / (peak_fp32 * 1e12),
+            "roofline_peak": "measured FP32 issue peak (of measured)",
             "blocks": info["blocks"],
             "max_team": info["max_team"], "graph": info["graph"],
             "plain": {"ms": plain_ms, "frame_pairs_per_s": n_pairs / (plain_ms * 1e-3),
                       "gpairs_per_s": plain_pe / (plain_ms * 1e-3) / 1e9},
-            "max_pose_diff_vs_plain": worst}
+            "max_pose_diff_vs_plain": worst,
+            "bf16": {"features": "BF16 appearance features (feat_bf16 = 1), FP32 pair arithmetic",
+                     "ms_per_batch": t_bf, "frame_pairs_per_s": n_pairs / (t_bf * 1e-3),
+                     "gpairs_per_s": pe_bf / (t_bf * 1e-3) / 1e9,
+                     "roofline_frac": pe_bf / (t_bf * 1e-3) * w_avg / (peak_fp32 * 1e12),
+                     "max_pose_diff_vs_fp32_batch":
+                         max(max(synth_pose_err(P_bf[i], P[i])) for i in range(n_pairs)),
+                     "failed": int(sum(1 for x in st_bf if x["status"] != 0))}}
 
 
-def _serve_trace(seconds):
-    trace = synth.serving_trace(n_streams=64, rate_hz=30.0, duration_s=seconds,
-                                n_range=(5000, 60000), keyframe_every=10)
-    kfs, frames = {}, []
-    for r in trace:
-        if r["kf_seed"] not in kfs:
-            kfs[r["kf_seed"]] = synth.stream_keyframe(r["kf_seed"], r["n_kf"])
-        frames.append(synth.stream_frame(r["kf_seed"], r["frame"], r["n"]))
-    prev = {}
-    for r in trace:   # the keyframe each keyframe replaces (to release it)
-        seq = prev.setdefault(r["stream"], [])
-        if not seq or seq[-1] != r["kf_seed"]:
-            r["replaces"] = seq[-1] if seq else None
-            seq.append(r["kf_seed"])
-        else:
-            r["replaces"] = None
-    return trace, kfs, frames
+def _dense_golden():
+    """The oracle's pose of the dense room pair and the checksums of the
+    inputs it was computed on (tests/golden/dense_room100k_pose.txt)."""
+    path = os.path.join(ROOT, "tests", "golden", "dense_room100k_pose.txt")
+    if not os.path.exists(path):
+        return None
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split(None, 1)
+        out[k] = v.strip()
+    out["P"] = np.array([float(x) for x in out["P"].split()]).reshape(4, 4)
+    return out
+
+
+def bench_dense(cvo, torch, local, flush, peak_fp32):
+    """Config 4: one dense room pair (95% of the valid pixels subsampled to
+    100,000 points per frame), the whole solve timed like the main line, its
+    per-pass roofline, and its pose against the oracle's own solve stored in
+    tests/golden (when this run's synthetic inputs match the stored ones)."""
+    d = synth.room_pair(n_points=100000, seed=synth.seed_for(4), mode="valid")
+    g = _dense_golden()
+    same = g is not None and all(
+        abs(float(np.sum(d[k], dtype=np.float64)) - float(g[f"sum_{k}"]))
+        <= 1e-9 * max(1.0, abs(float(g[f"sum_{k}"]))) for k in ("X", "FX", "Z", "FZ"))
+    wpp = work_per_pair(d["FX"].shape[1])
+    with cvo.Context(device=local) as ctx:
+        ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+        stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
+        ctx.align(ht, hs)
+        ms, outs = [], []
+        for _ in range(5):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0, e1 = _events(torch, stream)
+                e0.record(stream)
+            outs.append(ctx.align(ht, hs))
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        _, _, recs = ctx.align_profile(ht, hs)
+    t = statistics.median(ms)
+    P, st = outs[-1]
+    inst = (sum(r["grad_pairs"] for r in recs) * wpp["grad"]
+            + sum(r["step_pairs"] for r in recs) * wpp["step"])
+    return {"workload": "dense room pair: 95% of the valid pixels of two ray-cast 640x480 room "
+                        "frames subsampled to 100,000 points each, 3 deg / 3 cm motion",
+            "ms_per_solve": t, "frame_pairs_per_s": 1e3 / t,
+            "gpairs_per_s": st["pair_evals"] / (t * 1e-3) / 1e9, "iters": st["iters"],
+            "roofline_frac": inst / (t * 1e-3) / 1e12 / peak_fp32,
+            "per_pass": pass_roofline(recs, wpp, peak_fp32),
+            "pose_vs_truth": list(synth_pose_err(P, d["P_gt"])),
+            "pose_vs_oracle": list(synth_pose_err(P, g["P"])) if same else None,
+            "oracle_iters": int(g["iters"]) if same else None,
+            "oracle_pose": "tests/golden/dense_room100k_pose.txt (FP64 oracle solve, cell "
+                           "search)" if same else "not compared: this run's synthetic inputs "
+                                                  "differ from the stored ones"}
+
+
+class _FramePool:
+    """Frame content for the serving traces: the keyframe and the frames of a
+    request are drawn from a pool of n_kf keyframe epochs (textured planes,
+    5k-60k points each) with 10 frames each, picked by the request's keyframe
+    seed and frame index, so that long traces need not generate (and hold)
+    thousands of distinct clouds. Every keyframe of a trace is still uploaded
+    and released as its own resident cloud."""
+
+    def __init__(self, n_kf=32, keyframe_every=10, n_range=(5000, 60000), seed=None):
+        seed = synth.seed_for(5, 9) if seed is None else seed
+        rng = np.random.default_rng(seed)
+        self.n_kf = n_kf
+        self.kfs, self.frames = [], {}
+        for k in range(n_kf):
+            ks = seed * 1009 + k
+            self.kfs.append(synth.stream_keyframe(ks, int(rng.integers(n_range[0], n_range[1] + 1))))
+            for f in range(keyframe_every):
+                Z, FZ, _ = synth.stream_frame(ks, f, int(rng.integers(n_range[0], n_range[1] + 1)))
+                self.frames[(k, f)] = (Z, FZ)
+
+    def trace(self, seconds, rate_hz, n_streams=64, seed=None):
+        trace = synth.serving_trace(n_streams=n_streams, rate_hz=rate_hz, duration_s=seconds,
+                                    n_range=(5000, 60000), keyframe_every=10, seed=seed)
+        kfs, frames = {}, []
+        for r in trace:
+            k = r["kf_seed"] % self.n_kf
+            kfs.setdefault(r["kf_seed"], self.kfs[k])
+            frames.append(self.frames[(k, r["frame"])])
+        prev = {}
+        for r in trace:   # the keyframe each keyframe replaces (to release it)
+            seq = prev.setdefault(r["stream"], [])
+            if not seq or seq[-1] != r["kf_seed"]:
+                r["replaces"] = seq[-1] if seq else None
+                seq.append(r["kf_seed"])
+            else:
+                r["replaces"] = None
+        return trace, kfs, frames
 
 
 def _serve_run(cvo, trace, kfs, frames):
@@ -528,8 +732,13 @@ def _plain_run(cvo, trace, kfs, frames):
     return res, span
 
 
-def bench_serving(cvo, seconds):
-    trace, kfs, frames = _serve_trace(seconds)
+def bench_serving(cvo, seconds, load_seconds, long_seconds):
+    """The request loop against plain one-at-a-time solves on the same
+    open-loop traces: first the overload point (64 streams at 30 Hz), whose
+    served rate is taken as the loop's capacity; then offered loads of 0.5,
+    0.8 and 1.0 of that capacity, and a long run at 0.8. Latency runs from
+    arrival to result."""
+    pool = _FramePool()
 
     def summary(res, span):
         lat = np.array([x[2] * 1e3 for x in res])
@@ -538,14 +747,44 @@ def bench_serving(cvo, seconds):
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "failed": int(sum(1 for x in res if x[1]["status"] != 0))}
 
-    rs, ss = _serve_run(cvo, trace, kfs, frames)
-    rp, sp = _plain_run(cvo, trace, kfs, frames)
-    out = summary(rs, ss)
-    out["workload"] = (f"{len(trace)} requests: 64 streams x 30 Hz (Poisson) for {seconds} s, "
-                       f"planes frames 5k-60k points vs resident keyframes renewed every 10 frames")
+    def point(secs, rate_hz, seed=None):
+        trace, kfs, frames = pool.trace(secs, rate_hz, seed=seed)
+        rs, ss = _serve_run(cvo, trace, kfs, frames)
+        rp, sp = _plain_run(cvo, trace, kfs, frames)
+        out = {"requests": len(trace), "seconds_of_arrivals": secs,
+               "offered_frames_per_s": len(trace) / secs,
+               "served": summary(rs, ss), "plain": summary(rp, sp),
+               "max_pose_diff_vs_plain": max(max(synth_pose_err(a[0], b[0]))
+                                             for a, b in zip(rs, rp))}
+        out["served_beats_plain"] = {
+            "throughput": out["served"]["frame_pairs_per_s"] >= out["plain"]["frame_pairs_per_s"],
+            "p50": out["served"]["p50_ms"] <= out["plain"]["p50_ms"],
+            "p99": out["served"]["p99_ms"] <= out["plain"]["p99_ms"]}
+        return out
+
+    over = point(seconds, 30.0)
+    out = dict(over["served"])
+    out["plain"] = over["plain"]
+    out["max_pose_diff_vs_plain"] = over["max_pose_diff_vs_plain"]
+    out["workload"] = (f"{over['requests']} requests: 64 streams x 30 Hz (Poisson) for {seconds} s, "
+                       f"planes frames 5k-60k points vs resident keyframes renewed every 10 "
+                       f"frames (frame content from a pool of 32 keyframe epochs x 10 frames)")
     out["latency"] = "arrival to result, open loop (offered load above capacity: queueing included)"
-    out["plain"] = summary(rp, sp)
-    out["max_pose_diff_vs_plain"] = max(max(synth_pose_err(a[0], b[0])) for a, b in zip(rs, rp))
+    cap = over["served"]["frame_pairs_per_s"]
+    out["capacity_frames_per_s"] = cap
+    loads = []
+    for frac in (0.5, 0.8, 1.0):
+        p = point(load_seconds, frac * cap / 64.0, seed=synth.seed_for(5, int(frac * 10)))
+        p["load_of_capacity"] = frac
+        loads.append(p)
+    if long_seconds > 0:
+        p = point(long_seconds, 0.8 * cap / 64.0, seed=synth.seed_for(5, 80))
+        p["load_of_capacity"] = 0.8
+        p["long"] = True
+        loads.append(p)
+    over["load_of_capacity"] = "overload (64 streams x 30 Hz)"
+    loads.append(over)
+    out["loads"] = loads
     return out
 
 

@@ -305,58 +305,73 @@ def ell_floor(prm: Params) -> float:
     return 0.03 if prm.schedule == "table1" else float(prm.ell_min)
 
 
-def align(X, FX, Z, FZ, P0, prm: Params, record: bool = False) -> dict:
-    """Gradient ascent on F over SE(3) (Problem 1), one iteration being:
-    gradient at the current pose (Eq. 3_gradient scaled by Eq. metric),
-    step sums along it (Eq. fourth), the step length from the quartic, and
-    the update P <- exp(t xi) P (Eqs. newstep and step).
+def iterate(X, FX, Z, FZ, P0, prm: Params):
+    """The iterations of the solve (Problem 1) one at a time: a generator that
+    yields, after each iteration, a dict with the iteration's lengthscale,
+    F, gradient xi, step sums S, step length t, kept pairs of both passes,
+    the updated pose P and whether the stop test fired (``stop``). One
+    iteration is: gradient at the current pose (Eq. 3_gradient scaled by
+    Eq. metric), step sums along it (Eq. fourth), the step length from the
+    quartic, and the update P <- exp(t xi) P (Eqs. newstep and step).
 
-    Stops after the iteration at which the lengthscale sits at its floor and
-    either |t xi| < eps_pose or |xi| < eps_grad (Table 1), or after max_iters.
-    When the quartic has no maximiser on t > 0, the step is half the previous
-    one (1e-3/|xi| on the first iteration) and the iteration is counted in
-    ``fallback_steps``. When |xi| < eps_grad (below the gradient threshold of
-    Table 1's stop test) or S1 <= 0 (S1 is the metric norm of xi, so this
-    happens only when xi is at rounding level) no step is taken and the
-    iteration is counted in ``no_ascent_steps``: a xi at rounding level can
-    still give S1 > 0, and the quartic's root along it is then arbitrary.
+    It stops after the iteration at which the lengthscale sits at its floor
+    and either |t xi| < eps_pose or |xi| < eps_grad (Table 1), or after
+    max_iters. When the quartic has no maximiser on t > 0, the step is half
+    the previous one (1e-3/|xi| on the first iteration; ``fallback`` is set).
+    When |xi| < eps_grad (below the gradient threshold of Table 1's stop
+    test) or S1 <= 0 (S1 is the metric norm of xi, so this happens only when
+    xi is at rounding level) no step is taken (``no_ascent``): a xi at
+    rounding level can still give S1 > 0, and the quartic's root along it is
+    then arbitrary.
     """
     P = _c(P0).reshape(4, 4).copy()
     ells = ell_schedule(prm, prm.max_iters)
     floor = ell_floor(prm)
     t_prev = None
-    fallbacks = 0
-    no_ascent = 0
-    hist = []
-    nnz_total = 0
-    converged = False
-    it = 0
     for k in range(prm.max_iters):
         ell = ells[k]
         s = pair_sums(X, FX, Z, FZ, P, ell, prm)
         xi = gradient(s, prm)
         nxi = float(np.linalg.norm(xi))
         s2 = pair_sums(X, FX, Z, FZ, P, ell, prm, xi=xi)
-        nnz_total += s["nnz"] + s2["nnz"]
+        fallback = no_ascent = False
         if nxi == 0.0 or nxi < prm.eps_grad or not s2["S"][1] > 0.0:
             t = 0.0
-            no_ascent += 1
+            no_ascent = True
         else:
             t, ok = quartic_step(s2["S"], prm.step_order)
             if not ok:
-                fallbacks += 1
+                fallback = True
                 t = 0.5 * t_prev if t_prev is not None else 1e-3 / nxi
         P = exp_se3(t * xi) @ P
         t_prev = t
-        it = k + 1
+        stop = ell == floor and (abs(t) * nxi < prm.eps_pose or nxi < prm.eps_grad)
+        yield {"k": k, "ell": ell, "F": s["F"], "xi": xi, "t": t, "S": s2["S"],
+               "nnz": s["nnz"], "pairs": s["nnz"] + s2["nnz"], "P": P.copy(),
+               "fallback": fallback, "no_ascent": no_ascent, "stop": stop}
+        if stop:
+            return
+
+
+def align(X, FX, Z, FZ, P0, prm: Params, record: bool = False) -> dict:
+    """The whole solve (Problem 1): every iteration of ``iterate`` until its
+    stop test fires or max_iters is reached. Returns the final pose, the
+    iteration count, whether the stop test fired, the fallback and no-ascent
+    step counts, the kept pairs of every pass, and (record) the history."""
+    P = _c(P0).reshape(4, 4).copy()
+    res = {"P": P, "iters": 0, "converged": False, "fallback_steps": 0, "no_ascent_steps": 0,
+           "pair_evals": 0, "history": []}
+    for r in iterate(X, FX, Z, FZ, P0, prm):
+        res["P"] = r["P"]
+        res["iters"] = r["k"] + 1
+        res["converged"] = r["stop"]
+        res["fallback_steps"] += int(r["fallback"])
+        res["no_ascent_steps"] += int(r["no_ascent"])
+        res["pair_evals"] += r["pairs"]
         if record:
-            hist.append({"ell": ell, "F": s["F"], "xi": xi.copy(), "t": t, "S": s2["S"].copy(),
-                         "nnz": s["nnz"]})
-        if ell == floor and (abs(t) * nxi < prm.eps_pose or nxi < prm.eps_grad):
-            converged = True
-            break
-    return {"P": P, "iters": it, "converged": converged, "fallback_steps": fallbacks,
-            "no_ascent_steps": no_ascent, "pair_evals": nnz_total, "history": hist}
+            res["history"].append({"ell": r["ell"], "F": r["F"], "xi": r["xi"].copy(),
+                                   "t": r["t"], "S": r["S"].copy(), "nnz": r["nnz"]})
+    return res
 
 
 def pose_error(P_est, P_ref):
