@@ -367,6 +367,9 @@ int configure_plan(cvo_ctx* ctx, Plan* p, Cloud* t, Cloud* s, const std::vector<
     ic[k].rc2 = (float)rc2;
     ic[k].rprune = (float)(std::sqrt(rc2) * 1.001);
     ic[k].level = level_of[k];
+    ic[k].at_floor = ell == ell_floor(prm) ? 1 : 0;
+    ic[k].kf_rot = prm.sigma * prm.sigma / (ell2 * prm.a2);
+    ic[k].kf_tr = prm.sigma * prm.sigma / (ell2 * prm.b2);
     ic[k].filter = (mode == kModeEval ||
                     (k + 1 < ells.size() && ells[k + 1] == ell && level_of[k + 1] == level_of[k]))
                        ? 1 : 0;

@@ -82,6 +82,9 @@ struct IterConst {
   int filter;              // 1: a plan built at this iteration filters its candidates (the
                            //   next iteration keeps the lengthscale, so the plan is reused;
                            //   or an evaluation)
+  int at_floor;            // 1: ell is the schedule's floor (the stop test may fire)
+  double kf_rot, kf_tr;    // sigma^2 / (ell^2 a^2) and sigma^2 / (ell^2 b^2): the factors that
+                           //   turn the pair sums into the metric gradient (Eq. metric)
 };
 
 // Constant for one solve plan (device memory).

@@ -134,15 +134,25 @@ struct TailConst {
   int reduce_fp32;   // precision study: block and cross-block sums in FP32
   unsigned wait_polls;                 // barrier polls before a block gives up
   unsigned long long join_limit_ns;    // longest wait of a queued team's join
+  float cXf[3], inv_a2f, inv_b2f, src_radius_f;   // FP32 copies for the FP32 parts of the tail
 };
 
 struct BlockCtx {
   TailConst tc;
   double P[16];           // current pose
   double Rp[9], Tp[3];    // centred pose at the last plan
-  double xi[6];
-  double xi_norm, F;
-  double S[5];
+  double xi[6];           // metric gradient (Eq. metric)
+  double x0[6];           // its components before the metric factors (FP64 pair sums, centring
+                          // back-map applied)
+  double u64[6];          // xi / |xi|
+  double xi_norm, xi_inv, F;
+  double S[5];            // S0..S4 of the last step pass (formed when published)
+  double s_raw[5];        // the step pass's sums along xi / |xi| (S_m = s_m sigma^2 |xi|^m)
+  double kf_rot, kf_tr;   // this iteration's metric factors
+  int small_grad;         // |xi| below the gradient threshold (or zero): no step, stop test
+  int at_floor;           // this iteration's ell is the schedule's floor
+  int fin;                // step pass: warps done with their share (the first does the FP64
+                          // gradient)
   double t, t_prev;
   double ell, inv_l2, r_plan, plan_ell;
   int k, level, plan_level, plan_filter;
@@ -175,9 +185,58 @@ __device__ __forceinline__ double flip_sign(double v, bool neg) {
                               (neg ? (long long)0x8000000000000000ull : 0ll));
 }
 
+// Conversions and power-of-two scalings by integer operations on the bit
+// patterns. On GB300 every FP64 warp instruction (conversions and compares
+// included) holds the FP64 pipe for about 64 cycles, so the tails keep their
+// FP64 instruction count low and leave the rest to the integer and FP32 pipes.
+
+// x 2^shift truncated to FP32 (toward zero); magnitudes below FP32's normal
+// range give a signed zero, above it a signed infinity, a NaN stays a NaN.
+__device__ __forceinline__ float f64_to_f32_shift(double x, int shift) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  const unsigned sign = (unsigned)hi & 0x80000000u;
+  const unsigned m = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m != 0u || lo != 0u ? 0x400000u : 0u));
+  const int e32 = e - 1023 + 127 + shift;
+  if (e == 0 || e32 <= 0) return __uint_as_float(sign);
+  if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e32 << 23) | m);
+}
+
+__device__ __forceinline__ float f64_to_f32(double x) { return f64_to_f32_shift(x, 0); }
+
+// The exact FP64 value of an FP32 number (FP32 subnormals as zero).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned sign = u & 0x80000000u;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned e64 = e == 0xffu ? 0x7ffu : e - 127u + 1023u;
+  return __hiloint2double((int)(sign | (e64 << 20) | ((u & 0x7fffffu) >> 3)), (int)((u & 7u) << 29));
+}
+
+// x 2^k for k in [0, 8]: an exponent increment when x is normal and stays so.
+__device__ __forceinline__ double mul_pow2(double x, int k) {
+  const int hi = __double2hiint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  if (e > 0 && e + k < 0x7ff) return __hiloint2double(hi + (k << 20), __double2loint(x));
+  return x * (double)(1 << k);
+}
+
+// x > 0 (false for zero, negative values and NaN), from the bit pattern.
+__device__ __forceinline__ bool is_pos(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  if (hi < 0) return false;
+  if (((hi >> 20) & 0x7ff) == 0x7ff && ((hi & 0xfffff) != 0 || lo != 0u)) return false;
+  return hi != 0 || lo != 0u;
+}
+
 // Iteration k's constants (ic = the host table's entry k), the FP32 pose, and
 // whether the traversal plan must be rebuilt. Warp 0, every lane.
-__device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
+__device__ __noinline__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
   // centred pose [R T'] on lanes 0..11, element (r, c) = (l / 4, l % 4):
   // R = the pose's rotation, T' = R cZ + T - cX
   const int l = min(lane, 11), r = l >> 2, c = l & 3;
@@ -186,14 +245,15 @@ __device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
                             fma(b.P[4 * r], b.tc.cZ[0], b.P[4 * r + 3] - b.tc.cX[r])));
   const double v = c == 3 ? t3 : b.P[4 * r + c];
   // is the current plan still a superset of the pairs within the cutoff?
-  const double need = (double)ic.rprune;   // 1.001 r_c
+  const float need = ic.rprune;   // 1.001 r_c
   // reuse only at an unchanged lengthscale (the floor of the schedule): while
   // ell shrinks a fresh, tighter plan costs less than the extra candidates
-  bool replan = b.need_plan || ic.level != b.plan_level || ic.ell != b.plan_ell;
+  bool replan = b.need_plan || ic.level != b.plan_level ||
+                __double_as_longlong(ic.ell) != __double_as_longlong(b.plan_ell);
   if (!replan) {
-    // the differences in FP64, their squares summed in FP32 (the 1e-5
-    // relative margin below covers FP32 rounding)
-    const float d = (float)(v - (c == 3 ? b.Tp[r] : b.Rp[3 * r + c]));
+    // the differences in FP64, the rest in FP32: the 2e-5 relative and
+    // 1e-6 r_c margins below cover its rounding
+    const float d = f64_to_f32(v - (c == 3 ? b.Tp[r] : b.Rp[3 * r + c]));
     const float sq = lane < 12 ? d * d : 0.0f;
     float sr = c < 3 ? sq : 0.0f, st = c == 3 ? sq : 0.0f;
 #pragma unroll
@@ -204,14 +264,15 @@ __device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
     sr = __shfl_sync(kFull, sr, 0);
     st = __shfl_sync(kFull, st, 0);
     // |dR z + dT| <= |dR|_F |z| + |dT| for every source point, |z| <= r_src
-    const double drift = ((double)sqrtf(sr) * b.tc.src_radius + (double)sqrtf(st)) *
-                             (1.0 + 1e-5) + 1e-6 * need;
-    replan = (need + drift > b.r_plan) || (b.r_plan > kLoose * (need + drift));
+    const float drift = fmaf(sqrtf(sr), b.tc.src_radius_f, sqrtf(st)) * (1.0f + 2e-5f) + 1e-6f * need;
+    const float rp = b.rplan_f;
+    replan = (need + drift > rp) || (rp > (float)kLoose * (need + drift));
   }
   __syncwarp();   // every lane has read the old plan pose
   if (lane < 12) {
-    if (c < 3) b.R[3 * r + c] = (float)v;
-    else b.T[r] = (float)v;
+    // rounded to nearest: the passes' pose
+    if (c < 3) b.R[3 * r + c] = __double2float_rn(v);
+    else b.T[r] = __double2float_rn(v);
     if (replan) {
       if (c < 3) b.Rp[3 * r + c] = v;
       else b.Tp[r] = v;
@@ -224,12 +285,17 @@ __device__ void begin_iteration(const IterConst& ic, BlockCtx& b, int lane) {
     b.rc2 = ic.rc2;
     b.inv_l2f = (float)ic.inv_l2;
     b.level = ic.level;
+    b.kf_rot = ic.kf_rot;
+    b.kf_tr = ic.kf_tr;
+    b.at_floor = ic.at_floor;
     if (replan) {
       b.need_plan = 1;
       b.plan_level = ic.level;
       b.plan_ell = ic.ell;
       b.plan_filter = ic.filter;
-      b.r_plan = need * (1.0 + kSkin);
+      // the radius is FP32 throughout: (float)(need (1 + skin)) is what the
+      // plan and the passes use
+      b.r_plan = (double)need * (1.0 + kSkin);
       b.rplan_f = (float)b.r_plan;
     }
   }
@@ -279,32 +345,14 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
   const int e_max = max(max((__double2hiint(c0) >> 20) & 0x7ff, (__double2hiint(c1) >> 20) & 0x7ff),
                         max((__double2hiint(c2) >> 20) & 0x7ff, (__double2hiint(c3) >> 20) & 0x7ff));
   if (e_max == 0x7ff) return false;   // an infinity or a NaN
-  double sc;
-  if (e_max >= 2 && e_max <= 2044) {
-    // 2^(1022 - e_max): the largest magnitude lands in [0.5, 1)
-    sc = __hiloint2double((2045 - e_max) << 20, 0);
-  } else {
-    const double s = fmax(fmax(fabs(c0), fabs(c1)), fmax(fabs(c2), fabs(c3)));
-    if (!(s > 0.0)) return false;
-    // 2^-e with s = m 2^e, m in [0.5, 1) (subnormal s are scaled twice)
-    sc = 1.0;
-    double ss = s;
-    if (ss < 0x1p-1000) {
-      sc = 0x1p+1000;
-      ss *= sc;
-    }
-    const int ex = min(1000, ((__double2hiint(ss) >> 20) & 0x7ff) - 1022);
-    sc *= __hiloint2double((1023 - ex) << 20, 0);
-  }
-  c0 *= sc;
-  c1 *= sc;
-  c2 *= sc;
-  c3 *= sc;
   // start: a root of the cubic from the closed form, all in FP32 on the
-  // scaled coefficients (any root; the checks below decide whether it is the
-  // wanted one), refined by two FP32 Newton steps; a negligible cubic term is
-  // left out of the start only
-  const float f0 = (float)c0, f1 = (float)c1, f2 = (float)c2, f3 = (float)c3;
+  // coefficients scaled by 2^(1022 - e_max) (the largest has magnitude in
+  // [0.5, 1); formed from the bit patterns, truncated: a start needs no
+  // more), refined by two FP32 Newton steps; a negligible cubic term is left
+  // out of the start only
+  const int shift = 1022 - e_max;
+  const float f0 = f64_to_f32_shift(c0, shift), f1 = f64_to_f32_shift(c1, shift);
+  const float f2 = f64_to_f32_shift(c2, shift), f3 = f64_to_f32_shift(c3, shift);
   float ts = -1.0f;
   if (fabsf(f3) <= 1e-12f) {
     if (fabsf(f2) <= 1e-12f) {
@@ -351,28 +399,60 @@ __device__ bool first_maximiser(double c0, double c1, double c2, double c3, doub
     const float tn = ts - ff / fd;
     if (fd < 0.0f && tn > 0.0f && isfinite(tn)) ts = tn;
   }
-  const double t32 = (double)ts;
-  // fast path: one FP64 Newton step from that start, accepted when it moves t
-  // by at most 1e-6 t (the step squares the start's error) and G'' < 0 on
-  // [0, t] (then G' falls from c0 > 0 over [0, t], so t is its first root and
-  // a + -> - crossing)
-  if (ts > 0.0f && isfinite(ts)) {
+  const double t32 = f32_to_f64(ts);
+  // fast path: one FP64 Newton step from that start on the unscaled
+  // coefficients (the roots do not depend on a common scale), accepted when it
+  // moves t by at most 2^-20 t (the step squares the start's error) and
+  // G'' < 0 on [0, t] (then G' falls from c0 > 0 over [0, t], so t is its
+  // first root and a + -> - crossing). G''(0) = c1 < 0 is read from the sign
+  // bit; G''(t) < 0 and the vertex test of a concave G'' are evaluated in FP32
+  // on the scaled coefficients with a 1e-4 relative margin (their rounding is
+  // below 1e-6), and anything within the margin goes to the bracketed search.
+  if (e_max >= 2 && ts > 0.0f && isfinite(ts) && __double2hiint(c1) < 0) {
     const double f = fma(fma(fma(c3, t32, c2), t32, c1), t32, c0);
-    const double fp = fma(fma(3.0 * c3, t32, 2.0 * c2), t32, c1);
-    if (fp < 0.0) {
-      // 1/fp from FP32 and one FP64 Newton step (an fp outside FP32's range
-      // gives a non-finite t, which the checks reject)
-      const double t = fma(-f, recip_refined(fp), t32);
-      // G''(0) = c1 < 0, G''(t) < 0, and for concave G'' (c3 < 0) with its
-      // vertex -c2 / (3 c3) inside (0, t), the vertex value c1 - c2^2 / (3 c3) < 0
-      if (t > 0.0 && isfinite(t) && fabs(t - t32) <= 1e-6 * t && c1 < 0.0 &&
-          fma(fma(3.0 * c3, t, 2.0 * c2), t, c1) < 0.0 &&
-          (!(c3 < 0.0 && c2 > 0.0 && c2 < -3.0 * c3 * t) || 3.0 * c1 * c3 > c2 * c2)) {
+    const double fp = fma(fma(3.0 * c3, t32, mul_pow2(c2, 1)), t32, c1);
+    const int hfp = __double2hiint(fp), efp = (hfp >> 20) & 0x7ff;
+    if (hfp < 0 && efp > 1023 - 120 && efp < 1023 + 120) {
+      // 1/fp from FP32 and one FP64 Newton step
+      double r = f32_to_f64(1.0f / f64_to_f32(fp));
+      r = r * fma(-fp, r, 2.0);
+      const double dt = -f * r;
+      const double t = t32 + dt;
+      const int ht = __double2hiint(t), hd = __double2hiint(dt);
+      const int et = (ht >> 20) & 0x7ff, ed = (hd >> 20) & 0x7ff;
+      const bool settled = ed <= et - 21;   // |dt| < 2^-20 t (dt = 0 has ed = 0)
+      const float g2 = fmaf(fmaf(3.0f * f3, ts, 2.0f * f2), ts, f1);
+      const float gmag = fabsf(f1) + fabsf(2.0f * f2 * ts) + fabsf(3.0f * f3 * ts * ts);
+      const bool inside = f3 < 0.0f && f2 > 0.0f && f2 < -3.0f * f3 * ts * (1.0f + 1e-4f);
+      const bool vertex_ok = !inside || 3.0f * f1 * f3 > f2 * f2 * (1.0f + 1e-4f);
+      if (ht > 0 && et < 0x7ff && settled && g2 < -1e-4f * gmag && vertex_ok) {
         *t_out = t;
         return true;
       }
     }
   }
+  // the bracketed search, on the coefficients scaled by a power of two
+  double sc;
+  if (e_max >= 2 && e_max <= 2044) {
+    // 2^(1022 - e_max): the largest magnitude lands in [0.5, 1)
+    sc = __hiloint2double((2045 - e_max) << 20, 0);
+  } else {
+    const double s = fmax(fmax(fabs(c0), fabs(c1)), fmax(fabs(c2), fabs(c3)));
+    if (!(s > 0.0)) return false;
+    // 2^-e with s = m 2^e, m in [0.5, 1) (subnormal s are scaled twice)
+    sc = 1.0;
+    double ss = s;
+    if (ss < 0x1p-1000) {
+      sc = 0x1p+1000;
+      ss *= sc;
+    }
+    const int ex = min(1000, ((__double2hiint(ss) >> 20) & 0x7ff) - 1022);
+    sc *= __hiloint2double((1023 - ex) << 20, 0);
+  }
+  c0 *= sc;
+  c1 *= sc;
+  c2 *= sc;
+  c3 *= sc;
   if (fabs(c3) < 1e-30) c3 = 0.0;
   if (fabs(c2) < 1e-30) c2 = 0.0;
   // positive critical points of G', ascending
@@ -474,17 +554,49 @@ __constant__ double kExpSeries[3][7] = {
     {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800, -1.0 / 6227020800.0,
      1.0 / 1307674368000.0}};
 
-// Gradient tail: sums (F, omega', v, pairs, candidates) -> F, metric
-// gradient (lanes 0..5), unit step direction in the centred frame. Warp 0.
-__device__ void finish_gradient(BlockCtx& b, const double* sums, int lane) {
+// Gradient tail, first part (warp 0, between the gradient barrier and the
+// step pass): the unit step direction in the centred frame, in FP32, which is
+// all the step pass needs. Lane a < 6 holds component a of the gradient before
+// the metric factors, x0 = omega' + cX x v (rotation) or v (translation), in
+// FP64 (the centring back-map may cancel); the common factor sigma^2 / ell^2
+// drops out of the direction, so only 1/a^2 and 1/b^2 are applied. The FP64
+// gradient itself (gradient_fp64) is formed during the step pass.
+__device__ void gradient_direction(BlockCtx& b, const double* sums, int lane) {
   const TailConst& tc = b.tc;
-  const double kf = tc.sigma2 * b.inv_l2;
-  // component a of xi on lane a < 6: (omega'_a + (cX x v)_a) k_a or v_a k_b
   const int a = lane % 3, a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
   const bool rot = lane < 3;
   const double cr = fma(tc.cX[a1], sums[4 + a2], -(tc.cX[a2] * sums[4 + a1]));
   const double x0 = sums[1 + min(lane, 5)] + (rot ? cr : 0.0);
-  const double x = lane < 6 ? x0 * (kf * (rot ? tc.inv_a2 : tc.inv_b2)) : 0.0;
+  if (lane < 6) b.x0[lane] = x0;
+  const float x = lane < 6 ? __double2float_rn(x0) * (rot ? tc.inv_a2f : tc.inv_b2f) : 0.0f;
+  float nrm2 = x * x;
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) nrm2 += __shfl_xor_sync(kFull, nrm2, off);
+  nrm2 = __shfl_sync(kFull, nrm2, 0);
+  // 1/|x|: rsqrt and one Newton step (relative error about 1e-7)
+  float inv = 0.0f;
+  if (nrm2 > 0.0f && nrm2 < INFINITY) {
+    inv = rsqrtf(nrm2);
+    inv = inv * fmaf(-0.5f * nrm2, inv * inv, 1.5f);
+  }
+  // omega_a = x_a / |x|, v'_a = (v_a + (omega x cX)_a) / |x|
+  const float xa1 = __shfl_sync(kFull, x, a1), xa2 = __shfl_sync(kFull, x, a2);
+  const float xv = __shfl_sync(kFull, x, 3 + a);
+  const float vc = (xv + fmaf(xa1, tc.cXf[a2], -(xa2 * tc.cXf[a1]))) * inv;
+  if (lane < 3) {
+    b.om[a] = x * inv;
+    b.vc[a] = vc;
+  }
+  if (lane == 0) b.fin = 0;
+  __syncwarp();
+}
+
+// Gradient tail, second part (one warp, during the step pass; it writes only
+// fields the pass does not read): the metric gradient xi (Eq. metric), |xi|,
+// xi / |xi| in FP64, F and the gradient pass's counts.
+__device__ void gradient_fp64(BlockCtx& b, const double* sums, int lane) {
+  const TailConst& tc = b.tc;
+  const double x = lane < 6 ? b.x0[lane] * (lane < 3 ? b.kf_rot : b.kf_tr) : 0.0;
   double nrm2 = x * x;
 #pragma unroll
   for (int off = 4; off > 0; off >>= 1) nrm2 += __shfl_xor_sync(kFull, nrm2, off);
@@ -492,27 +604,23 @@ __device__ void finish_gradient(BlockCtx& b, const double* sums, int lane) {
   // |xi| and 1/|xi|: FP32 rsqrt refined by an FP64 Newton step
   // y <- y (1.5 - 0.5 x y^2) (relative error 1e-7 -> 1e-14)
   double inv = 0.0, nrm = 0.0;
-  const float r32 = nrm2 > 0.0 && nrm2 < 1e30 ? rsqrtf((float)nrm2) : 0.0f;
-  if (r32 > 0.0f && isfinite(r32)) {
-    inv = (double)r32;
+  const int e2 = (__double2hiint(nrm2) >> 20) & 0x7ff;
+  if (__double2hiint(nrm2) >= 0 && e2 > 1023 - 100 && e2 < 1023 + 100) {
+    inv = f32_to_f64(rsqrtf(f64_to_f32(nrm2)));
     inv = inv * fma(-0.5 * nrm2, inv * inv, 1.5);
     nrm = nrm2 * inv;
   } else if (nrm2 > 0.0) {
     nrm = sqrt(nrm2);
     inv = 1.0 / nrm;
   }
-  // unit direction: omega_a = xi_a / |xi|, v'_a = (v_a + (omega x cX)_a) / |xi|
-  const double xa1 = __shfl_sync(kFull, x, a1), xa2 = __shfl_sync(kFull, x, a2);
-  const double xv = __shfl_sync(kFull, x, 3 + a);
-  const double vc = (xv + fma(xa1, tc.cX[a2], -(xa2 * tc.cX[a1]))) * inv;
-  const double om = x * inv;
-  if (lane < 6) b.xi[lane] = x;
-  if (lane < 3) {
-    b.om[a] = (float)om;
-    b.vc[a] = (float)vc;
+  if (lane < 6) {
+    b.xi[lane] = x;
+    b.u64[lane] = x * inv;
   }
   if (lane == 0) {
     b.xi_norm = nrm;
+    b.xi_inv = inv;
+    b.small_grad = (!(nrm > 0.0) || nrm < tc.eps_grad) ? 1 : 0;
     b.F = tc.sigma2 * sums[0];
     b.nnz_grad = (unsigned long long)__double_as_longlong(sums[7]);
     b.cand_grad = (unsigned long long)__double_as_longlong(sums[8]);
@@ -520,65 +628,79 @@ __device__ void finish_gradient(BlockCtx& b, const double* sums, int lane) {
   __syncwarp();
 }
 
-// Step tail: S0..S4, step length, pose update P <- exp(t xi) P, stop test.
-// Warp 0.
+// S0..S4 of the last step pass (Eq. fourth along xi): the pass summed along
+// xi / |xi|, so S_m = s_m sigma^2 |xi|^m. Formed for the published results
+// only. Any thread.
+__device__ __forceinline__ void form_step_sums(BlockCtx& b) {
+  double pw = b.tc.sigma2;
+  for (int m = 0; m < 5; ++m) {
+    b.S[m] = b.s_raw[m] * pw;
+    pw *= b.xi_norm;
+  }
+}
+
+// Step tail: step length, pose update P <- exp(t xi) P, stop test. Warp 0.
+// The step length is found in tau = |xi| t, the step along xi / |xi|: G'(t) =
+// sum_m m S_m t^(m-1) = sigma^2 |xi| sum_m m s_m tau^(m-1), so the quartic of
+// the pass's own sums has the same roots in tau (no powers of |xi| needed),
+// and the twist is tau (xi / |xi|).
 __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
   const TailConst& tc = b.tc;
-  const double nxi = b.xi_norm;
-  // S_m = sums_m sigma^2 |xi|^m on lane m < 5 (the sums were taken along xi / |xi|)
-  const int m = min(lane, 4);
-  const double n2 = nxi * nxi;
-  double pw = (m & 1) ? nxi : 1.0;
-  if (m & 2) pw *= n2;
-  if (m & 4) pw *= n2 * n2;
-  const double Sm = sums[m] * (tc.sigma2 * pw);
-  const double S1 = __shfl_sync(kFull, Sm, 1), S2 = __shfl_sync(kFull, Sm, 2);
-  const double S3 = __shfl_sync(kFull, Sm, 3), S4 = __shfl_sync(kFull, Sm, 4);
-  if (lane < 5) b.S[lane] = Sm;
+  if (lane < 5) b.s_raw[lane] = sums[lane];
   if (lane == 0) {
     b.nnz_total += b.nnz_grad + (unsigned long long)__double_as_longlong(sums[5]);
     b.cand_total += b.cand_grad + (unsigned long long)__double_as_longlong(sums[6]);
   }
   if (tc.mode == kModeEval) {
-    if (lane == 0) b.done = 1;
+    __syncwarp();
+    if (lane == 0) {
+      form_step_sums(b);
+      b.done = 1;
+    }
     __syncwarp();
     return;
   }
   // the step length (the same scalar work on every lane)
-  double t;
+  double tau;
   int no_ascent = 0, fallback = 0;
   // no step along a gradient below the stop test's threshold (at rounding
-  // level S1 can still be positive, and the quartic's root is then arbitrary)
-  if (!(nxi > 0.0) || nxi < tc.eps_grad || !(S1 > 0.0)) {
-    t = 0.0;
+  // level S1 can still be positive, and the quartic's root is then arbitrary);
+  // S1 > 0 exactly when s1 > 0
+  if (b.small_grad || !is_pos(sums[1])) {
+    tau = 0.0;
     no_ascent = 1;
   } else {
     bool ok;
     if (tc.step_order == 2) {
-      ok = S2 < 0.0;
-      t = ok ? -S1 / (2.0 * S2) : 0.0;
+      ok = sums[2] < 0.0;
+      tau = ok ? -sums[1] / mul_pow2(sums[2], 1) : 0.0;
     } else {
-      ok = first_maximiser(S1, 2.0 * S2, 3.0 * S3, 4.0 * S4, &t);
+      ok = first_maximiser(sums[1], mul_pow2(sums[2], 1), 3.0 * sums[3], mul_pow2(sums[4], 2),
+                           &tau);
     }
     if (!ok) {
       fallback = 1;
-      t = b.have_t_prev ? 0.5 * b.t_prev : 1e-3 / nxi;
+      // half the previous step, or 1e-3 / |xi| on the first one (tau = 1e-3)
+      tau = b.have_t_prev ? 0.5 * b.t_prev * b.xi_norm : 1e-3;
     }
   }
-  // twist t xi: rotation phi (lanes 0..2), translation rho (lanes 3..5)
-  const double tw = t * b.xi[min(lane, 5)];
+  // twist tau xi / |xi|: rotation phi (lanes 0..2), translation rho (lanes 3..5)
+  const double tw = tau * b.u64[min(lane, 5)];
   const double p0 = __shfl_sync(kFull, tw, 0), p1 = __shfl_sync(kFull, tw, 1);
   const double p2 = __shfl_sync(kFull, tw, 2);
   const double r0 = __shfl_sync(kFull, tw, 3), r1 = __shfl_sync(kFull, tw, 4);
   const double r2 = __shfl_sync(kFull, tw, 5);
   const double x = fma(p0, p0, fma(p1, p1, p2 * p2));
-  // A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3 on lanes 0, 1, 2
+  // A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3 on lanes 0, 1, 2.
+  // The series alternate with falling terms, so the first term left out
+  // bounds the error: 1 term below x = 1e-16, 2 below 1e-8, 3 below 1e-5, 4
+  // below 1e-3 (errors below 1e-17 relative), all 7 below 0.25.
   double coef;
   if (x < 0.25) {
     const double* k = kExpSeries[min(lane, 2)];
-    coef = k[6];
-#pragma unroll
-    for (int i = 5; i >= 0; --i) coef = fma(coef, x, k[i]);
+    const int n = x < 1e-16 ? 0 : x < 1e-8 ? 1 : x < 1e-5 ? 2 : x < 1e-3 ? 3 : 6;
+    coef = k[n];
+    for (int i = n - 1; i >= 0; --i) coef = fma(coef, x, k[i]);
   } else {
     const double th = sqrt(x);
     const double sn = sin(th), hs = sin(0.5 * th);
@@ -614,11 +736,12 @@ __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
   if (lane == 0) {
     b.no_ascent += no_ascent;
     b.fallback += fallback;
+    const double t = tau * b.xi_inv;
     b.t = t;
     b.t_prev = t;
     b.have_t_prev = 1;
-    const bool conv = (b.ell == tc.ell_floor) &&
-                      (fabs(t) * nxi < tc.eps_pose || nxi < tc.eps_grad);
+    // Table 1: |t xi| = |tau| below eps_pose, or |xi| below eps_grad, at the floor
+    const bool conv = b.at_floor && (fabs(tau) < tc.eps_pose || b.small_grad);
     b.k += 1;
     if (conv || b.k >= tc.max_iters) {
       b.done = 1;
@@ -627,6 +750,7 @@ __device__ void finish_step(BlockCtx& b, const double* sums, int lane) {
   }
   __syncwarp();
 }
+
 
 // The team barrier counts arrivals on one counter that is never reset during
 // a launch: generation g is complete when (g + 1) * nblk blocks have arrived.
@@ -1742,6 +1866,13 @@ __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* pa
   unsigned nnz = 0, cand = 0;
   pass_warp<STEP, DP, MODE, DPS, NU>(cfg, sm, warp, lane, cache, slots, acc, nnz, cand);
   __syncwarp();
+  if (STEP) {
+    // the first warp done with its share forms the FP64 gradient (it reads
+    // the gradient totals, which stay in place until the step barrier)
+    int first = 0;
+    if (lane == 0) first = atomicAdd(&sm.b.fin, 1) == 0 ? 1 : 0;
+    if (__shfl_sync(kFull, first, 0)) gradient_fp64(sm.b, sm.sums, lane);
+  }
 #pragma unroll
   for (int i = 0; i < NACC; ++i) {
     const float v = warp_sum_f(acc[i]);
@@ -1777,7 +1908,8 @@ __device__ void run_pass(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, double* pa
   }
 }
 
-__device__ void publish(SolveState* st, const BlockCtx& b) {
+__device__ void publish(SolveState* st, BlockCtx& b) {
+  form_step_sums(b);
   for (int i = 0; i < 16; ++i) st->P[i] = b.P[i];
   for (int i = 0; i < 6; ++i) st->xi[i] = b.xi[i];
   for (int i = 0; i < 5; ++i) st->S[i] = b.S[i];
@@ -1830,6 +1962,10 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     tc.reduce_fp32 = cfg->reduce_fp32;
     tc.wait_polls = cfg->wait_polls;
     tc.join_limit_ns = cfg->join_limit_ns;
+    for (int a = 0; a < 3; ++a) tc.cXf[a] = (float)cfg->cX[a];
+    tc.inv_a2f = (float)(1.0 / cfg->a2);
+    tc.inv_b2f = (float)(1.0 / cfg->b2);
+    tc.src_radius_f = (float)cfg->src_radius * (1.0f + 1e-6f);
     for (int i = 0; i < 16; ++i) b.P[i] = st->P0[i];
     b.k = 0;
     b.team_rank = team.rank;
@@ -1909,7 +2045,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     if (stamp) tg2 = globaltimer();
     if (warp == 0) {
       if (lane == 0) sm.b.collect_kept = 0;
-      finish_gradient(sm.b, sm.sums, lane);
+      gradient_direction(sm.b, sm.sums, lane);
     }
     __syncthreads();
     if (stamp) t2 = globaltimer();
