@@ -61,6 +61,11 @@ constexpr double kSkin = 0.10;              // plan radius margin (fraction of t
 constexpr double kLoose = 1.25;             // replan when the plan radius exceeds this factor
 constexpr int kFilterMax = 1024;            // candidates of a cluster the plan filters at most
 constexpr int kActChunks = 32;              // chunks per cluster whose source-group activity is kept
+// teams of at most this many blocks box-test the candidates of unfiltered
+// clusters in the streamed passes (their warps' shares are long runs of
+// chunks); larger teams, whose shares are short and whose work split counts
+// unfiltered candidates, stream them unfiltered
+constexpr int kCompactTeamMax = 32;
 #ifndef CVO_COST_ACTIVE
 #define CVO_COST_ACTIVE 12
 #endif
@@ -159,6 +164,7 @@ struct BlockCtx {
   int need_plan, done, converged, fallback, no_ascent, have_t_prev;
   int use_kept, collect_kept, rebalance;   // kept-pair weighting of the work split
   int use_act;                             // the split weighs source groups by their activity
+  int compact;                             // streamed passes box-test unfiltered clusters
   int team_rank, team_size;                // this block's place in its team (read after a pass
                                            // from shared memory rather than kept in registers)
   unsigned long long nnz_total, cand_total, nnz_grad, cand_grad;
@@ -1077,8 +1083,10 @@ __device__ void plan_cluster(const SolveCfg* cfg, const BlockCtx& b, SolveState*
     cfg->cl_cand[c] = total;
     cfg->cl_fcand[c] = t0 + t1;
     cfg->cl_kept[c] = 0;
-    cfg->cl_box[2 * (size_t)c] = lo4;
-    cfg->cl_box[2 * (size_t)c + 1] = hi4;
+    // the box at the plan pose, whether or not the plan filtered (w = 1: the
+    // segment offsets count the candidates within the plan radius of it)
+    cfg->cl_box[2 * (size_t)c] = make_float4(blo[0], blo[1], blo[2], filt ? 1.f : 0.f);
+    cfg->cl_box[2 * (size_t)c + 1] = make_float4(bhi[0], bhi[1], bhi[2], 0.f);
   }
 }
 
@@ -1628,9 +1636,85 @@ __device__ void pass_stream(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
     FCursor cur = fcursor_at<DPS, NU>(sm, warp, nseg, jb * 32);
     const int want = min(fc, 32 * (je + 1)) - 32 * jb;
     const unsigned nnz0 = nnz;
-    if (lo.x == -INFINITY) {
-      // an unfiltered cluster: chunk j holds candidates 32 j .. 32 j + 31,
-      // loaded straight into registers, the next chunk's while this one runs
+    if (lo.w == 0.f && !collect && b.compact) {
+      // a cluster the plan did not filter (a plan used for one iteration):
+      // the candidates of the range's chunks go through the box test here
+      // and the survivors are compacted through the ring into full chunks
+      // of all source groups. A chunk the range shares with the neighbouring
+      // warp (it starts or ends at a source group inside it) runs unfiltered
+      // with its own groups, as the plan's numbering of chunks assigns it.
+      const int G = cs4 >> 2;
+      int glo_b, ghi_b, glo_e, ghi_e;
+      range_groups(r, c, jb, G, glo_b, ghi_b);
+      range_groups(r, c, je, G, glo_e, ghi_e);
+      const bool head = glo_b > 0 || ghi_b < G;
+      const bool tail = je != jb && ghi_e < G;
+      const auto raw_chunk = [&](int j, int glo, int ghi) {
+        FCursor cj = fcursor_at<DPS, NU>(sm, warp, nseg, j * 32);
+        float xf[DPS];
+        const float4 xp =
+            load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, j * 32 + lane, tc, cj.seg, xf);
+        if (glo < ghi) {
+          const int jlo = 4 * glo, jhi = min(cs4, 4 * ghi);
+          if (j * 32 + lane < tc) cand += (unsigned)max(0, min(cs, jhi) - jlo);
+          chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, jlo, jhi, rc2, A, acc, nnz);
+        }
+      };
+      if (head) raw_chunk(jb, glo_b, ghi_b);
+      const int j0 = head ? jb + 1 : jb, j1 = tail ? je - 1 : je;
+      if (j0 <= j1) {
+        const int uend = min(tc, 32 * (j1 + 1));
+        // a cursor at raw candidate 32 j0 (its segment from the offsets, which
+        // count every candidate here), nothing to skip
+        FCursor cf = fcursor_at<DPS, NU>(sm, warp, nseg, j0 * 32);
+        cf.u = j0 * 32;
+        cf.skip = 0;
+        float xfn[DPS];
+        float4 xpn = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, cf.u + lane, uend,
+                                                                cf.seg, xfn);
+        int used = 0;
+        for (;;) {
+          // place blocks of 32 until a chunk is full or the range is done (at
+          // most 63 entries are unread, so the ring never overwrites one)
+          while (cf.made - used < 32 && cf.u < uend) {
+            const int o = fplace(cf, xpn, lo, hi, rp2, lane, uend);
+            if (o >= 0) {
+              const int e = o & 63;
+              rxyz[e] = xpn;
+#pragma unroll
+              for (int d = 0; d < DP; ++d) rfeat[d * 64 + e] = xfn[d];
+            }
+            if (cf.u < uend)
+              xpn = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, cf.u + lane, uend,
+                                                               cf.seg, xfn);
+          }
+          const int cnt = min(32, cf.made - used);
+          if (cnt <= 0) break;
+          __syncwarp();
+          float4 xp = make_float4(-kFar, -kFar, -kFar, 0.f);
+          float xf[DPS];
+#pragma unroll
+          for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
+          if (lane < cnt) {
+            const int e = (used + lane) & 63;
+            xp = rxyz[e];
+#pragma unroll
+            for (int d = 0; d < DP; ++d) xf[d] = rfeat[d * 64 + e];
+            cand += (unsigned)cs;
+          }
+          __syncwarp();   // read before the next placement reuses the entries
+          chunk_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, xp, xf, 0, cs4, rc2, A, acc, nnz);
+          used += cnt;
+        }
+      }
+      if (tail) raw_chunk(je, glo_e, ghi_e);
+      continue;
+    }
+    if (lo.w == 0.f) {
+      // an unfiltered cluster whose first gradient pass records which source
+      // groups kept pairs, chunk by chunk: chunk j holds candidates 32 j ..
+      // 32 j + 31, loaded straight into registers, the next chunk's while this
+      // one runs
       float xfn[DPS];
       float4 xpn = load_candidate<DP, DPS, NU, bf16_of(MODE)>(g, sm, warp, jb * 32 + lane, tc,
                                                               cur.seg, xfn);
@@ -1762,8 +1846,12 @@ __device__ void fill_cache(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp
     }
     ++n;
     const int nseg = load_segments<DPS, NU>(cfg, sm, warp, lane, c, tc, fc);
-    const float4 lo = __ldcg(&cfg->cl_box[2 * (size_t)c]);
-    const float4 hi = __ldcg(&cfg->cl_box[2 * (size_t)c + 1]);
+    float4 lo = __ldcg(&cfg->cl_box[2 * (size_t)c]);
+    float4 hi = __ldcg(&cfg->cl_box[2 * (size_t)c + 1]);
+    if (lo.w == 0.f) {   // not filtered by the plan: every candidate of the range is cached
+      lo = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+      hi = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    }
     FCursor cur = fcursor_at<DPS, NU>(sm, warp, nseg, jb * 32);
     const int want = min(fc, 32 * (je + 1)) - 32 * jb;
     float* s0 = base + (size_t)n * slot_floats<DP>();
@@ -1977,6 +2065,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
     b.done = cfg->max_iters <= 0 ? 1 : 0;
     b.converged = b.fallback = b.no_ascent = b.have_t_prev = 0;
     b.use_kept = b.collect_kept = b.rebalance = b.use_act = 0;
+    b.compact = team.size <= kCompactTeamMax ? 1 : 0;
     b.t = b.t_prev = 0.0;
     b.nnz_total = b.cand_total = b.nnz_grad = b.cand_grad = 0;
     b.F = b.xi_norm = 0.0;
