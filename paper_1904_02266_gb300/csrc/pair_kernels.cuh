@@ -300,8 +300,10 @@ __device__ __noinline__ void begin_iteration(const IterConst& ic, BlockCtx& b, i
       b.plan_ell = ic.ell;
       b.plan_filter = ic.filter;
       // the radius is FP32 throughout: (float)(need (1 + skin)) is what the
-      // plan and the passes use
-      b.r_plan = (double)need * (1.0 + kSkin);
+      // plan and the passes use. A plan used for one iteration sees only
+      // that iteration's pose (the pose moves at its end and the next
+      // iteration re-plans at a new lengthscale), so it needs no skin
+      b.r_plan = (double)need * (ic.filter ? 1.0 + kSkin : 1.0);
       b.rplan_f = (float)b.r_plan;
     }
   }
