@@ -1053,6 +1053,24 @@ int cvo_batch_create(cvo_ctx* ctx, int n, const int32_t* targets, const int32_t*
   for (int i = 0; i < n; ++i) b->order[i] = i;
   std::stable_sort(b->order.begin(), b->order.end(),
                    [&](int a, int c) { return work[a] > work[c]; });
+  // The last pairs of the queue (the last 10% of the estimated work) get
+  // teams four times larger: a pair takes about as long as the others on its
+  // team (sizes follow the work), so when the queue runs dry the blocks would
+  // otherwise wait up to one pair's time for the last teams to finish; larger
+  // teams finish those pairs sooner (256-pair batch: 527 -> 570
+  // frame-pairs/s; 5% x 2: 528, 10% x 2: 561, 15% x 3: 567, 20% x 4: 562,
+  // 20% x 8: 557, 30% x 4: 556)
+  if (!team_sizes) {
+    constexpr double kTailWork = 0.10;
+    constexpr int kTailBoost = 4;
+    double tail = 0.0;
+    for (int q = n - 1; q >= 0; --q) {
+      const int i = b->order[q];
+      tail += work[i];
+      if (tail > kTailWork * total) break;
+      b->team[i] = std::min(nblocks, b->team[i] * kTailBoost);
+    }
+  }
   int rc = dev_alloc(ctx, (void**)&b->d_states, sizeof(SolveState) * n, &b->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&b->d_entries, sizeof(QueueEntry) * n, &b->bytes);
   if (rc == CVO_OK) rc = dev_alloc(ctx, (void**)&b->d_ctl, sizeof(BatchCtl), &b->bytes);
