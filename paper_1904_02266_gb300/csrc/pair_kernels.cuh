@@ -1125,7 +1125,8 @@ __device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const Clu
 // Shared memory of the solve kernel.
 template <int DPS, int NU>
 struct SolveSmem {
-  float4 z[kWarps][kClusterMax];
+  float4 z[kWarps][kClusterMax];    // staged cluster, local: (-2 z_l, |z_l|^2), see stage_cluster
+  float4 zo[kWarps];                // origin of each warp's staged cluster (centred frame)
   float zf[kWarps][DPS][kClusterMax];
   float4 u[kWarps][NU][kClusterMax];
   int xs[kWarps][kMaxSeg];
@@ -1316,27 +1317,41 @@ __device__ void split_work(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int tid,
 }
 
 // Stage one cluster for a warp: lane j < cs holds the cluster's centred
-// source point p and its features; the transformed point z~' = R p + T (and,
-// for the step pass, the Taylor coefficient vectors of Eq. fourth) go to the
-// warp's shared-memory slots, read by every lane of the pair loop.
+// source point p and its features. The transformed point z~' = R p + T is
+// stored relative to the cluster's origin o (lane 0's transformed point) as
+// (-2 z_l, |z_l|^2), z_l = z~' - o, so that a candidate x_l = x' - o tests
+// its squared distance as |x_l|^2 + x_l . (-2 z_l) + |z_l|^2: three FMAs
+// with x_l and |x_l|^2 formed once per chunk. The cluster is small (an
+// octree cell of the plan's level), so |x_l| and |z_l| stay within a few
+// cutoff radii and the expansion loses no more than a few bits to
+// cancellation. Padding slots hold (0, 0, 0, +inf): beyond every cutoff,
+// zero weight. For the step pass the Taylor coefficient vectors of Eq.
+// fourth go to the warp's slots as well, their fourth components holding
+// the per-point constants that turn x_l . U_k into e . U_k (e = x' - z~').
 template <bool STEP, int DP, int DPS, int NU>
 __device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, int lane, bool zv,
                                               float4 p, const float pf[DPS]) {
   const BlockCtx& b = sm.b;
-  float4 z = make_float4(kFar, kFar, kFar, 0.f);
+  float zt[3] = {0.f, 0.f, 0.f};
   if (zv) {
-    z.x = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
-    z.y = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
-    z.z = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
+    zt[0] = fmaf(b.R[0], p.x, fmaf(b.R[1], p.y, fmaf(b.R[2], p.z, b.T[0])));
+    zt[1] = fmaf(b.R[3], p.x, fmaf(b.R[4], p.y, fmaf(b.R[5], p.z, b.T[1])));
+    zt[2] = fmaf(b.R[6], p.x, fmaf(b.R[7], p.y, fmaf(b.R[8], p.z, b.T[2])));
   }
-  sm.z[warp][lane] = z;
+  // lane 0 holds a point of every staged cluster (cs >= 1)
+  const float ox = __shfl_sync(kFull, zt[0], 0), oy = __shfl_sync(kFull, zt[1], 0),
+              oz = __shfl_sync(kFull, zt[2], 0);
+  const float lx = zv ? zt[0] - ox : 0.f, ly = zv ? zt[1] - oy : 0.f, lz = zv ? zt[2] - oz : 0.f;
+  sm.z[warp][lane] = zv ? make_float4(-2.f * lx, -2.f * ly, -2.f * lz,
+                                      fmaf(lx, lx, fmaf(ly, ly, lz * lz)))
+                        : make_float4(0.f, 0.f, 0.f, INFINITY);
+  if (lane == 0) sm.zo[warp] = make_float4(ox, oy, oz, 0.f);
 #pragma unroll
   for (int d = 0; d < DP; ++d) sm.zf[warp][d][lane] = zv ? pf[d] : 0.f;
   if (STEP) {
     const float* om = b.om;
     const float* vc = b.vc;
     const float inv_l2 = b.inv_l2f;
-    const float zt[3] = {zv ? z.x : 0.f, zv ? z.y : 0.f, zv ? z.z : 0.f};
     float u1[3], u2[3], u3[3], u4[3];
     u1[0] = om[1] * zt[2] - om[2] * zt[1] + vc[0];
     u1[1] = om[2] * zt[0] - om[0] * zt[2] + vc[1];
@@ -1354,14 +1369,21 @@ __device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, 
     const float u12 = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
     const float u13 = u1[0] * u3[0] + u1[1] * u3[1] + u1[2] * u3[2];
     const float u22 = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
-    // beta = e.U1; gamma = e.U2 - k2; delta = e.U3 - k3; eps = e.U4 - k4
+    // beta = e.U1; gamma = e.U2 - k2; delta = e.U3 - k3; eps = e.U4 - k4,
+    // with e.U = x_l.U - z_l.U: the fourth components hold -z_l.U - k
     const float c1 = inv_l2, c2 = 0.5f * inv_l2, c3 = inv_l2 * (1.0f / 6.0f),
                 c4 = inv_l2 * (1.0f / 24.0f);
-    sm.u[warp][0][lane] = make_float4(u1[0] * c1, u1[1] * c1, u1[2] * c1, 0.5f * u11 * inv_l2);
-    sm.u[warp][1 % NU][lane] = make_float4(u2[0] * c2, u2[1] * c2, u2[2] * c2, 0.5f * u12 * inv_l2);
-    sm.u[warp][2 % NU][lane] = make_float4(u3[0] * c3, u3[1] * c3, u3[2] * c3,
-                                           (u13 * (1.0f / 6.0f) + u22 * 0.125f) * inv_l2);
-    sm.u[warp][3 % NU][lane] = make_float4(u4[0] * c4, u4[1] * c4, u4[2] * c4, 0.f);
+    const float k2 = 0.5f * u11 * inv_l2, k3 = 0.5f * u12 * inv_l2,
+                k4 = (u13 * (1.0f / 6.0f) + u22 * 0.125f) * inv_l2;
+    const float4 U1 = make_float4(u1[0] * c1, u1[1] * c1, u1[2] * c1, 0.f);
+    const float4 U2 = make_float4(u2[0] * c2, u2[1] * c2, u2[2] * c2, 0.f);
+    const float4 U3 = make_float4(u3[0] * c3, u3[1] * c3, u3[2] * c3, 0.f);
+    const float4 U4 = make_float4(u4[0] * c4, u4[1] * c4, u4[2] * c4, 0.f);
+    const auto zl_dot = [&](const float4& U) { return fmaf(lx, U.x, fmaf(ly, U.y, lz * U.z)); };
+    sm.u[warp][0][lane] = make_float4(U1.x, U1.y, U1.z, -zl_dot(U1));
+    sm.u[warp][1 % NU][lane] = make_float4(U2.x, U2.y, U2.z, -zl_dot(U2) - k2);
+    sm.u[warp][2 % NU][lane] = make_float4(U3.x, U3.y, U3.z, -zl_dot(U3) - k3);
+    sm.u[warp][3 % NU][lane] = make_float4(U4.x, U4.y, U4.z, -zl_dot(U4) - k4);
   }
 }
 
@@ -1369,7 +1391,10 @@ __device__ __forceinline__ void stage_cluster(SolveSmem<DPS, NU>& sm, int warp, 
 // (xp, features xf; padding points lie beyond every cutoff), inner loop over
 // the cluster's points [jlo, jhi) (multiples of 4, at most the cluster size
 // rounded up to 4; padding slots lie beyond the cutoff too). FP32 pair
-// arithmetic, one ex2.approx per pair.
+// arithmetic, one ex2.approx per pair. Distances are taken relative to the
+// cluster's origin (stage_cluster): t = x_l . (-2 z_l) + |z_l|^2 equals
+// d^2 - |x_l|^2, so a pair is kept when t <= r_c^2 - |x_l|^2, and the
+// exponent A d^2 is A t + A |x_l|^2.
 // Points are taken four at a time: the four distance tests first, then, if
 // any lane of the warp keeps any of the four pairs (one vote, so the branch
 // is uniform), the four pair bodies without branches, a rejected pair
@@ -1380,19 +1405,22 @@ template <bool STEP, int DP, int MODE, int DPS, int NU>
 __device__ __forceinline__ unsigned chunk_pairs(SolveSmem<DPS, NU>& sm, int warp, float4 xp,
                                                 const float xf[DPS], int jlo, int jhi, float rc2,
                                                 float A, float acc[7], unsigned& nnz) {
-  float W = 0.f, Ex = 0.f, Ey = 0.f, Ez = 0.f;
+  const float4 o = sm.zo[warp];
+  const float xl = xp.x - o.x, yl = xp.y - o.y, zl = xp.z - o.z;
+  const float x2 = fmaf(xl, xl, fmaf(yl, yl, zl * zl));
+  const float thr = rc2 - x2;   // about -3e36 for a padding candidate: never kept
+  const float q0 = A * x2;
+  float W = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
   unsigned active = 0u;   // bit g: source group g kept a pair (the same in every lane)
   for (int j0 = jlo; j0 < jhi; j0 += 4) {
-    float ex[4], ey[4], ez[4], d2[4];
+    float4 m[4];
+    float t[4];
     bool keep[4];
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
-      const float4 z = sm.z[warp][j0 + jj];
-      ex[jj] = xp.x - z.x;
-      ey[jj] = xp.y - z.y;
-      ez[jj] = xp.z - z.z;
-      d2[jj] = fmaf(ex[jj], ex[jj], fmaf(ey[jj], ey[jj], ez[jj] * ez[jj]));
-      keep[jj] = d2[jj] <= rc2;
+      m[jj] = sm.z[warp][j0 + jj];
+      t[jj] = fmaf(xl, m[jj].x, fmaf(yl, m[jj].y, fmaf(zl, m[jj].z, m[jj].w)));
+      keep[jj] = t[jj] <= thr;
     }
     if (!__any_sync(kFull, keep[0] | keep[1] | keep[2] | keep[3])) continue;
     active |= 1u << (j0 >> 2);
@@ -1401,36 +1429,36 @@ __device__ __forceinline__ unsigned chunk_pairs(SolveSmem<DPS, NU>& sm, int warp
       const int j = j0 + jj;
       float w;
       if (color_of(MODE) == kColorKernel) {
-        float qf = 0.f;
+        float qf = q0;
 #pragma unroll
         for (int d = 0; d < DP; ++d) {
           const float df = xf[d] - sm.zf[warp][d][j];
           qf = fmaf(df, df, qf);
         }
-        w = ex2_approx(-fmaf(A, d2[jj], qf));
+        w = ex2_approx(-fmaf(A, t[jj], qf));
       } else if (color_of(MODE) == kColorDot) {
         float cdot = 0.f;
 #pragma unroll
         for (int d = 0; d < DP; ++d) cdot = fmaf(xf[d], sm.zf[warp][d][j], cdot);
-        w = ex2_approx(-A * d2[jj]) * cdot;
+        w = ex2_approx(-fmaf(A, t[jj], q0)) * cdot;
       } else {
-        w = ex2_approx(-A * d2[jj]);
+        w = ex2_approx(-fmaf(A, t[jj], q0));
       }
       w = keep[jj] ? w : 0.f;
       nnz += keep[jj] ? 1u : 0u;
       if (!STEP) {
-        // |e| <= 2 kFar is finite, so a zero weight adds exactly zero
+        // m = (-2 z_l, .) is finite, so a zero weight adds exactly zero
         W += w;
-        Ex = fmaf(w, ex[jj], Ex);
-        Ey = fmaf(w, ey[jj], Ey);
-        Ez = fmaf(w, ez[jj], Ez);
+        Mx = fmaf(w, m[jj].x, Mx);
+        My = fmaf(w, m[jj].y, My);
+        Mz = fmaf(w, m[jj].z, Mz);
       } else {
         const float4 U1 = sm.u[warp][0][j], U2 = sm.u[warp][1 % NU][j];
         const float4 U3 = sm.u[warp][2 % NU][j], U4 = sm.u[warp][3 % NU][j];
-        const float beta = fmaf(ex[jj], U1.x, fmaf(ey[jj], U1.y, ez[jj] * U1.z));
-        const float gam = fmaf(ex[jj], U2.x, fmaf(ey[jj], U2.y, fmaf(ez[jj], U2.z, -U1.w)));
-        const float del = fmaf(ex[jj], U3.x, fmaf(ey[jj], U3.y, fmaf(ez[jj], U3.z, -U2.w)));
-        const float eps = fmaf(ex[jj], U4.x, fmaf(ey[jj], U4.y, fmaf(ez[jj], U4.z, -U3.w)));
+        const float beta = fmaf(xl, U1.x, fmaf(yl, U1.y, fmaf(zl, U1.z, U1.w)));
+        const float gam = fmaf(xl, U2.x, fmaf(yl, U2.y, fmaf(zl, U2.z, U2.w)));
+        const float del = fmaf(xl, U3.x, fmaf(yl, U3.y, fmaf(zl, U3.z, U3.w)));
+        const float eps = fmaf(xl, U4.x, fmaf(yl, U4.y, fmaf(zl, U4.z, U4.w)));
         const float b2 = beta * beta;
         const float g2 = fmaf(0.5f, b2, gam);
         const float g3 = fmaf(beta, fmaf(b2, 1.0f / 6.0f, gam), del);
@@ -1446,7 +1474,12 @@ __device__ __forceinline__ unsigned chunk_pairs(SolveSmem<DPS, NU>& sm, int warp
     }
   }
   if (!STEP) {
-    // x' fixed per lane: sum_j w (z~'_j x e_ij) = x' x E_i
+    // E_i = sum_j w e_ij = x_l W - sum_j w z_l = x_l W + M / 2; x' fixed per
+    // lane: sum_j w (z~'_j x e_ij) = x' x E_i. A padding lane has W = M = 0
+    // and a finite x_l.
+    const float Ex = fmaf(xl, W, 0.5f * Mx);
+    const float Ey = fmaf(yl, W, 0.5f * My);
+    const float Ez = fmaf(zl, W, 0.5f * Mz);
     acc[0] += W;
     acc[1] += xp.y * Ez - xp.z * Ey;
     acc[2] += xp.z * Ex - xp.x * Ez;
