@@ -91,6 +91,24 @@ def test_eval_planes(cvo, mode, ell):
             _check_eval(g, d["X"], FX, d["Z"], FZ, P, ell, prm, f"{mode} {ell}")
 
 
+@pytest.mark.parametrize("cell_factor,cluster_factor", [(8.0, 8.0), (0.5, 1.0)])
+def test_eval_extreme_cell_and_cluster_factors(cvo, cell_factor, cluster_factor):
+    """The pair test runs in each cluster's own frame, so its cancellation grows
+    with the cluster's extent in cutoff radii; at the largest cell and cluster
+    factors the API accepts (clusters tens of r_c wide) and at the smallest,
+    F, the gradient, the kept pairs and the step sums still meet the parity bars."""
+    d = synth.planes_pair(3000, 3000, seed=synth.seed_for(1, 21))
+    with _ctx(cvo, cell_factor=cell_factor, cluster_factor=cluster_factor) as ctx:
+        prm = _oracle_params(ctx.params, cvo)
+        ht, hs = ctx.set_cloud(d["X"], d["FX"]), ctx.set_cloud(d["Z"], d["FZ"])
+        rng = np.random.default_rng(23)
+        for ell in (0.15, 0.05, 0.02):
+            for P in (d["P_gt"], synth.random_motion(rng, 2.0, 0.02) @ d["P_gt"]):
+                g = ctx.eval(ht, hs, P, ell)
+                _check_eval(g, d["X"], d["FX"], d["Z"], d["FZ"], P, ell, prm,
+                            f"cells {cell_factor} clusters {cluster_factor} ell {ell}")
+
+
 def _bf16_stored(F, scale):
     """The features the library keeps in BF16 mode: the FP32 product f * scale
     rounded to BF16 (nearest, ties to even), expressed back in feature units."""
