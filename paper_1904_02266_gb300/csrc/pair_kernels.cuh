@@ -1122,6 +1122,30 @@ __device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const Clu
   return w;
 }
 
+// Entries of a warp's pair list (build_lists): what one block per SM leaves
+// of shared memory for the widths whose cache slots it does not reduce.
+template <int DPS>
+__host__ __device__ constexpr int list_max() {
+  return DPS == 5 ? 640 : DPS == 1 ? 400 : 448;
+}
+constexpr int kListShift = 22;   // cache_cl of a listed cluster slot: cluster | length << 22
+static_assert(kMaxPoints <= (1 << kListShift), "cluster index must fit below the list length");
+
+// Per warp: the cell-row segments of the cluster being staged from the plan
+// (plan, cache fill, streamed passes), or, for a warp whose share is cached
+// from a plan that will be reused, its pair list (the segments are not needed
+// once the cache is filled, and a cached warp never streams).
+struct WarpSeg {
+  int xs[kMaxSeg];
+  int pf[kMaxSeg + 1];
+  int fpf[kMaxSeg + 1];   // filtered offsets (the plan: per-segment counts)
+};
+template <int DPS>
+union WarpScratch {
+  WarpSeg seg;
+  unsigned short list[list_max<DPS>()];
+};
+
 // Shared memory of the solve kernel.
 template <int DPS, int NU>
 struct SolveSmem {
@@ -1129,9 +1153,7 @@ struct SolveSmem {
   float4 zo[kWarps];                // origin of each warp's staged cluster (centred frame)
   float zf[kWarps][DPS][kClusterMax];
   float4 u[kWarps][NU][kClusterMax];
-  int xs[kWarps][kMaxSeg];
-  int pf[kWarps][kMaxSeg + 1];
-  int fpf[kWarps][kMaxSeg + 1];     // filtered offsets (the plan: per-segment counts)
+  WarpScratch<DPS> ws[kWarps];      // cell-row segments of the staged cluster, or the pair list
   float red[kWarps][10];
   double red_d[kWarps][16];
   long long scan[kThreads];
@@ -1143,7 +1165,8 @@ struct SolveSmem {
   int q_entry;                      //        entry that slot belongs to
   short cache_n[kWarps];            // slots cached per warp (-1: streamed)
   unsigned short cache_hdr[kWarps][32];
-  int cache_cl[kWarps][32];         // cluster of each cached cluster slot
+  int cache_cl[kWarps][32];         // cluster of each cached cluster slot (a listed one: | list
+                                    //   length << kListShift), chunk index of a chunk slot
   BlockCtx b;
 };
 
@@ -1524,13 +1547,13 @@ __device__ __forceinline__ int load_segments(const SolveCfg* cfg, SolveSmem<DPS,
                                              int lane, int c, int tc, int fc) {
   const int nseg = __ldcg(&cfg->cl_nseg[c]);
   for (int i = lane; i < nseg; i += 32) {
-    sm.xs[warp][i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
-    sm.pf[warp][i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
-    sm.fpf[warp][i] = __ldcg(&cfg->seg_fpref[(size_t)c * kMaxSeg + i]);
+    sm.ws[warp].seg.xs[i] = __ldcg(&cfg->seg_xs[(size_t)c * kMaxSeg + i]);
+    sm.ws[warp].seg.pf[i] = __ldcg(&cfg->seg_pref[(size_t)c * kMaxSeg + i]);
+    sm.ws[warp].seg.fpf[i] = __ldcg(&cfg->seg_fpref[(size_t)c * kMaxSeg + i]);
   }
   if (lane == 0) {
-    sm.pf[warp][nseg] = tc;
-    sm.fpf[warp][nseg] = fc;
+    sm.ws[warp].seg.pf[nseg] = tc;
+    sm.ws[warp].seg.fpf[nseg] = fc;
   }
   __syncwarp();
   return nseg;
@@ -1544,8 +1567,8 @@ __device__ __forceinline__ float4 load_candidate(const GridView& g, SolveSmem<DP
 #pragma unroll
   for (int d = 0; d < DPS; ++d) xf[d] = 0.f;
   if (q < tc) {
-    while (sm.pf[warp][seg + 1] <= q) ++seg;
-    const int xi = sm.xs[warp][seg] + (q - sm.pf[warp][seg]);
+    while (sm.ws[warp].seg.pf[seg + 1] <= q) ++seg;
+    const int xi = sm.ws[warp].seg.xs[seg] + (q - sm.ws[warp].seg.pf[seg]);
     xp = g.xyz[xi];
 #pragma unroll
     for (int d = 0; d < DP; ++d) xf[d] = load_feat<FB>(g.feat, (size_t)d * g.n_pad + xi);
@@ -1570,12 +1593,12 @@ __device__ __forceinline__ FCursor fcursor_at(const SolveSmem<DPS, NU>& sm, int 
   int lo = 0, hi = nseg;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (sm.fpf[warp][mid] <= f0) lo = mid;
+    if (sm.ws[warp].seg.fpf[mid] <= f0) lo = mid;
     else hi = mid;
   }
   FCursor cur;
-  cur.u = sm.pf[warp][lo];
-  cur.skip = f0 - sm.fpf[warp][lo];
+  cur.u = sm.ws[warp].seg.pf[lo];
+  cur.skip = f0 - sm.ws[warp].seg.fpf[lo];
   cur.seg = lo;
   cur.made = 0;
   return cur;
@@ -1832,10 +1855,78 @@ __device__ void pass_stream(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
 // plan (at the lengthscale floor, most of the solve) read no global memory.
 constexpr int kCacheSlots = 32;                 // header capacity per warp
 constexpr unsigned short kSlotCluster = 0x8000;
+constexpr unsigned short kSlotList = 0x4000;      // cluster slot whose pairs are listed
 
 template <int DP>
 __device__ __forceinline__ constexpr int slot_floats() {
   return 32 * (4 + DP);
+}
+
+// Pair lists of a plan that will be reused (Verlet-style): for each cached
+// cluster, the (candidate, source point) pairs of its cached chunks within
+// the plan radius at the plan pose, in slot order and, within a chunk, source
+// point by source point. While the plan is valid every source point stays
+// within the skin of where it was at the plan pose (the drift test of
+// begin_iteration), so these pairs are a superset of the pairs within the
+// cutoff, and the passes evaluate only them (each with the exact cutoff test)
+// instead of every candidate against every source group. An entry is
+// candidate lane | slot << 5 | source point << 10; the lists live in the
+// warp's shared scratch (list_max entries). A cluster whose list would not
+// fit keeps the chunk-by-chunk evaluation.
+template <int DP, int DPS, int NU>
+__device__ void build_lists(SolveSmem<DPS, NU>& sm, int warp, int lane, const float* base,
+                            int n) {
+  unsigned short* pl = sm.ws[warp].list;
+  constexpr int kCap = list_max<DPS>();
+  const BlockCtx& b = sm.b;
+  float R[9], T[3];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) R[i] = __double2float_rn(b.Rp[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) T[i] = __double2float_rn(b.Tp[i]);
+  const float rp2 = b.rplan_f * b.rplan_f;
+  const unsigned lt = (1u << lane) - 1u;
+  int run = 0;
+  for (int s = 0; s < n; ++s) {
+    const unsigned h = sm.cache_hdr[warp][s];
+    if (!(h & kSlotCluster)) continue;
+    const int cs = (int)(h & 0x3f);
+    const float4 p = reinterpret_cast<const float4*>(base + (size_t)s * slot_floats<DP>())[lane];
+    const float zx = fmaf(R[0], p.x, fmaf(R[1], p.y, fmaf(R[2], p.z, T[0])));
+    const float zy = fmaf(R[3], p.x, fmaf(R[4], p.y, fmaf(R[5], p.z, T[1])));
+    const float zz = fmaf(R[6], p.x, fmaf(R[7], p.y, fmaf(R[8], p.z, T[2])));
+    const int start = run;
+    bool fits = true;
+    int t = s + 1;
+    for (; t < n && !(sm.cache_hdr[warp][t] & kSlotCluster); ++t) {
+      const unsigned hc = sm.cache_hdr[warp][t];
+      const int cnt = (int)(hc & 0x3f);
+      const int jlo = 4 * (int)((hc >> 6) & 0xf), jhi = min(cs, 4 * (int)((hc >> 10) & 0xf));
+      const float4 xp =
+          reinterpret_cast<const float4*>(base + (size_t)t * slot_floats<DP>())[lane];
+      const bool valid = lane < cnt;
+      for (int j = jlo; j < jhi && fits; ++j) {
+        const float dx = xp.x - __shfl_sync(kFull, zx, j);
+        const float dy = xp.y - __shfl_sync(kFull, zy, j);
+        const float dz = xp.z - __shfl_sync(kFull, zz, j);
+        const bool in = valid && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= rp2;
+        const unsigned m = __ballot_sync(kFull, in);
+        if (run + __popc(m) > kCap) {
+          fits = false;   // warp-uniform
+        } else {
+          if (in) pl[run + __popc(m & lt)] = (unsigned short)(lane | (t << 5) | (j << 10));
+          run += __popc(m);
+        }
+      }
+    }
+    if (!fits) run = start;
+    if (lane == 0 && fits) {
+      sm.cache_hdr[warp][s] = (unsigned short)(h | kSlotList);
+      sm.cache_cl[warp][s] |= (run - start) << kListShift;
+    }
+    s = t - 1;
+  }
+  __syncwarp();
 }
 
 template <int DP, int MODE, int DPS, int NU>
@@ -1922,6 +2013,113 @@ __device__ void fill_cache(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int warp
   }
   if (lane == 0) sm.cache_n[warp] = (short)n;
   __syncwarp();
+  if (b.plan_filter) build_lists<DP, DPS, NU>(sm, warp, lane, base, n);
+}
+
+// One entry of a cluster's pair list (build_lists) against the staged
+// cluster: lane = one (candidate, source point) pair, with the same FP32
+// arithmetic as chunk_pairs (the same cutoff test on the same values, so the
+// same pairs are kept, and the same weight), the gradient sums formed per pair
+// (e = x_l - z_l, z~' x e = x' x e). Returns the kept flag.
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ __forceinline__ bool list_pair(SolveSmem<DPS, NU>& sm, int warp, const float* base,
+                                          float4 o, unsigned e, bool valid, float rc2, float A,
+                                          float acc[7], unsigned& nnz) {
+  const int k = (int)(e & 31u), t = (int)((e >> 5) & 31u), j = (int)(e >> 10);
+  const float* sl = base + (size_t)t * slot_floats<DP>();
+  const float4 xp = reinterpret_cast<const float4*>(sl)[k];
+  const float4 m = sm.z[warp][j];
+  const float xl = xp.x - o.x, yl = xp.y - o.y, zl = xp.z - o.z;
+  const float x2 = fmaf(xl, xl, fmaf(yl, yl, zl * zl));
+  const float thr = rc2 - x2;
+  const float q0 = A * x2;
+  const float tt = fmaf(xl, m.x, fmaf(yl, m.y, fmaf(zl, m.z, m.w)));
+  const bool keep = valid && tt <= thr;
+  float w;
+  if (color_of(MODE) == kColorKernel) {
+    float qf = q0;
+#pragma unroll
+    for (int d = 0; d < DP; ++d) {
+      const float df = sl[128 + d * 32 + k] - sm.zf[warp][d][j];
+      qf = fmaf(df, df, qf);
+    }
+    w = ex2_approx(-fmaf(A, tt, qf));
+  } else if (color_of(MODE) == kColorDot) {
+    float cdot = 0.f;
+#pragma unroll
+    for (int d = 0; d < DP; ++d) cdot = fmaf(sl[128 + d * 32 + k], sm.zf[warp][d][j], cdot);
+    w = ex2_approx(-fmaf(A, tt, q0)) * cdot;
+  } else {
+    w = ex2_approx(-fmaf(A, tt, q0));
+  }
+  w = keep ? w : 0.f;
+  nnz += keep ? 1u : 0u;
+  if (!STEP) {
+    // e = x_l - z_l = x_l + m / 2; every term is finite, so w = 0 adds zero
+    const float ex = fmaf(0.5f, m.x, xl), ey = fmaf(0.5f, m.y, yl), ez = fmaf(0.5f, m.z, zl);
+    acc[0] += w;
+    acc[1] = fmaf(w, xp.y * ez - xp.z * ey, acc[1]);
+    acc[2] = fmaf(w, xp.z * ex - xp.x * ez, acc[2]);
+    acc[3] = fmaf(w, xp.x * ey - xp.y * ex, acc[3]);
+    acc[4] = fmaf(w, ex, acc[4]);
+    acc[5] = fmaf(w, ey, acc[5]);
+    acc[6] = fmaf(w, ez, acc[6]);
+  } else {
+    const float4 U1 = sm.u[warp][0][j], U2 = sm.u[warp][1 % NU][j];
+    const float4 U3 = sm.u[warp][2 % NU][j], U4 = sm.u[warp][3 % NU][j];
+    const float beta = fmaf(xl, U1.x, fmaf(yl, U1.y, fmaf(zl, U1.z, U1.w)));
+    const float gam = fmaf(xl, U2.x, fmaf(yl, U2.y, fmaf(zl, U2.z, U2.w)));
+    const float del = fmaf(xl, U3.x, fmaf(yl, U3.y, fmaf(zl, U3.z, U3.w)));
+    const float eps = fmaf(xl, U4.x, fmaf(yl, U4.y, fmaf(zl, U4.z, U4.w)));
+    const float b2 = beta * beta;
+    const float g2 = fmaf(0.5f, b2, gam);
+    const float g3 = fmaf(beta, fmaf(b2, 1.0f / 6.0f, gam), del);
+    const float g4 = fmaf(b2 * b2, 1.0f / 24.0f, fmaf(0.5f * gam, b2 + gam, fmaf(beta, del, eps)));
+    acc[0] += w;
+    acc[1] = keep ? fmaf(w, beta, acc[1]) : acc[1];
+    acc[2] = keep ? fmaf(w, g2, acc[2]) : acc[2];
+    acc[3] = keep ? fmaf(w, g3, acc[3]) : acc[3];
+    acc[4] = keep ? fmaf(w, g4, acc[4]) : acc[4];
+  }
+  return keep;
+}
+
+// A listed cluster (staged): its nl pairs, 64 per round (two per lane, whose
+// chains overlap), the next round's entries loading while this one runs. In
+// the plan's first gradient pass (collect) the source groups of each chunk that
+// kept a pair are gathered per slot: lane t holds slot t's mask in act.
+template <bool STEP, int DP, int MODE, int DPS, int NU>
+__device__ void list_pairs(SolveSmem<DPS, NU>& sm, int warp, int lane, const float* base,
+                           const unsigned short* pl, int nl, float rc2, float A, float acc[7],
+                           unsigned& nnz, unsigned& cand, bool collect, unsigned& act) {
+  const float4 o = sm.zo[warp];
+  unsigned e0 = lane < nl ? pl[lane] : 0u, e1 = lane + 32 < nl ? pl[lane + 32] : 0u;
+  for (int r = 0; r < nl; r += 64) {
+    const bool v0 = r + lane < nl, v1 = r + 32 + lane < nl;
+    const unsigned c0 = e0, c1 = e1;
+    e0 = r + 64 + lane < nl ? pl[r + 64 + lane] : 0u;
+    e1 = r + 96 + lane < nl ? pl[r + 96 + lane] : 0u;
+    cand += (v0 ? 1u : 0u) + (v1 ? 1u : 0u);
+    const bool k0 = list_pair<STEP, DP, MODE, DPS, NU>(sm, warp, base, o, c0, v0, rc2, A, acc, nnz);
+    const bool k1 = list_pair<STEP, DP, MODE, DPS, NU>(sm, warp, base, o, c1, v1, rc2, A, acc, nnz);
+    if (collect) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool kk = h ? k1 : k0;
+        const unsigned ee = h ? c1 : c0;
+        const int ts = (int)((ee >> 5) & 31u);
+        const unsigned bit = 1u << (ee >> 12);   // source group j / 4
+        unsigned pend = __ballot_sync(kFull, kk);
+        while (pend) {
+          const int sl = __shfl_sync(kFull, ts, __ffs(pend) - 1);
+          const bool mine = kk && ts == sl;
+          const unsigned bits = __reduce_or_sync(kFull, mine ? bit : 0u);
+          if (lane == sl) act |= bits;
+          pend &= ~__ballot_sync(kFull, mine);
+        }
+      }
+    }
+  }
 }
 
 // The same share as pass_stream, from the warp's cache.
@@ -1932,8 +2130,9 @@ __device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
   const float rc2 = sm.b.rc2, A = sm.b.A;
   const bool collect = !STEP && sm.b.collect_kept;
   const float* base = cache + (size_t)warp * slots * slot_floats<DP>();
+  const unsigned short* pl = sm.ws[warp].list;
   const int n = sm.cache_n[warp];
-  int cs = 0, cs4 = 0, cur = -1;
+  int cs = 0, cs4 = 0, cur = -1, loff = 0;
   unsigned nnz0 = nnz;
   for (int s = 0; s < n; ++s) {
     const unsigned h = sm.cache_hdr[warp][s];
@@ -1947,12 +2146,30 @@ __device__ void pass_cached(const SolveCfg* cfg, SolveSmem<DPS, NU>& sm, int war
         add_kept(cfg, cur, nnz - nnz0, lane);
         nnz0 = nnz;
       }
-      cur = sm.cache_cl[warp][s];
+      cur = sm.cache_cl[warp][s] & ((1 << kListShift) - 1);
       __syncwarp();   // every lane is done with the previous cluster
       cs = (int)(h & 0x3f);
       stage_cluster<STEP, DP, DPS, NU>(sm, warp, lane, lane < cs, p, f);
       cs4 = (cs + 3) & ~3;
       __syncwarp();
+      if (h & kSlotList) {
+        // the cluster's chunks through its pair list, then past its chunk slots
+        int t = s + 1;
+        while (t < n && !(sm.cache_hdr[warp][t] & kSlotCluster)) ++t;
+        const int nl = (int)((unsigned)sm.cache_cl[warp][s] >> kListShift);
+        unsigned act = 0u;
+        list_pairs<STEP, DP, MODE, DPS, NU>(sm, warp, lane, base, pl + loff, nl, rc2, A, acc, nnz,
+                                            cand, collect, act);
+        loff += nl;
+        if (collect && lane > s && lane < t && act && cur >= 0) {
+          const int j = sm.cache_cl[warp][lane];
+          if (j < kActChunks) {
+            atomicOr(&cfg->ch_act[(size_t)cur * kActChunks + j], act);
+            atomicAdd(&cfg->cl_act[cur], __popc(act));
+          }
+        }
+        s = t - 1;
+      }
     } else {
       const int cnt = (int)(h & 0x3f);
       const int jlo = 4 * (int)((h >> 6) & 0xf), jhi = min(cs4, 4 * (int)((h >> 10) & 0xf));
@@ -2131,7 +2348,7 @@ __device__ void solve_pair(const SolveCfg* __restrict__ cfg, SolveState* __restr
       const ClusterView& cv = cfg->clusters[sm.b.level];
       if (replan) {
         for (long long c = gw; c < cv.ncl; c += NW)
-          plan_cluster(cfg, sm.b, st, (int)c, lane, sm.xs[warp], sm.pf[warp], sm.fpf[warp]);
+          plan_cluster(cfg, sm.b, st, (int)c, lane, sm.ws[warp].seg.xs, sm.ws[warp].seg.pf, sm.ws[warp].seg.fpf);
         if (!grid_sync(st, gen, &sm.flag, team.size, sm.b.tc.wait_polls)) break;
       }
       if (tid == 0) {
