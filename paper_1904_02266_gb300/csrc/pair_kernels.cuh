@@ -35,7 +35,10 @@
 // The plan is reused while it still covers the cutoff: it is built with a
 // radius 10% wider than the cutoff and rebuilt when the grid level changes,
 // when the pose has drifted by more than that margin (an FP64 bound over the
-// whole source cloud), or when it has become much wider than needed.
+// whole source cloud), or when it has become much wider than needed. A warp
+// whose share of a reused plan fits its cache slots also lists, once per
+// plan, the (candidate, source point) pairs of each cached cluster within the
+// plan radius, and its passes evaluate the lists instead of whole chunks.
 #pragma once
 
 #include <cuda_bf16.h>
