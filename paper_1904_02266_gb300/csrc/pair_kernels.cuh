@@ -1125,8 +1125,10 @@ __device__ __forceinline__ long long cluster_work(const SolveCfg* cfg, const Clu
   return w;
 }
 
-// Entries of a warp's pair list (build_lists): what one block per SM leaves
-// of shared memory for the widths whose cache slots it does not reduce.
+// Entries of a warp's pair list (build_lists), per padded feature width: as
+// many as fit beside the block's other static shared memory without taking a
+// cache slot from the dynamic part at one block per SM (640 at 5 feature
+// planes, 448 at 3 and 8, 400 without features).
 template <int DPS>
 __host__ __device__ constexpr int list_max() {
   return DPS == 5 ? 640 : DPS == 1 ? 400 : 448;
