@@ -157,7 +157,10 @@ int cvo_destroy(cvo_ctx* ctx);
  * float32 (ignored, may be NULL, when feat_dim == 0 or color_mode is NONE).
  * The library centres the cloud on its FP64 centroid, packs it
  * structure-of-arrays, orders it along a Morton curve for use as a source, and
- * builds the target cell lists lazily. Errors: CVO_ERR_INVALID_ARG for n <= 0,
+ * builds the target cell lists lazily. It returns once xyz and feat have been
+ * read (the caller may reuse them); the packing and ordering finish in order
+ * on the context's stream, before any later call uses the cloud, so a fault
+ * there would be reported by that later call. Errors: CVO_ERR_INVALID_ARG for n <= 0,
  * n > 2^22, NULL pointers or any non-finite value (checked on the device);
  * CVO_ERR_OUT_OF_BUDGET if the copy would exceed the budget. */
 int cvo_set_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, uint32_t flags,

@@ -469,9 +469,11 @@ namespace cvo {
 
 // Upload, check, centre, pack and Morton-order one cloud (the caller holds
 // the context lock). xyz / feat are host arrays, or device arrays read on
-// stream us when on_dev.
+// stream us when on_dev. The input is read before it returns (the statistics
+// are waited for); with wait the packing and ordering have finished too, else
+// they finish in order on the context stream, ahead of any later use.
 int create_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, bool on_dev,
-                 cudaStream_t us, Cloud** out) {
+                 cudaStream_t us, Cloud** out, bool wait) {
   *out = nullptr;
   if (!xyz) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL xyz pointer");
   if (n <= 0 || n > kMaxPoints) return fail(ctx, CVO_ERR_INVALID_ARG, "point count out of range");
@@ -552,7 +554,7 @@ int create_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, b
   if (raw_xyz) cudaFreeAsync(raw_xyz, ctx->stream);
   if (raw_feat) cudaFreeAsync(raw_feat, ctx->stream);
   raw_xyz = raw_feat = nullptr;
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && wait) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cleanup(fail(ctx, CVO_ERR_CUDA, cudaGetErrorString(e)));
   *out = c;
   return CVO_OK;
@@ -710,8 +712,10 @@ int cvo_set_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, 
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!handle_out) return fail(ctx, CVO_ERR_INVALID_ARG, "NULL handle pointer");
   Cloud* c = nullptr;
+  // the caller's arrays are read before this returns; the packing and ordering
+  // complete on the context stream, ahead of every later use of the cloud
   const int rc = create_cloud(ctx, xyz, feat, n, (flags & CVO_DEVICE_PTR) != 0,
-                              (cudaStream_t)stream, &c);
+                              (cudaStream_t)stream, &c, false);
   if (rc != CVO_OK) return rc;
   *handle_out = add_cloud(ctx, c);
   return CVO_OK;

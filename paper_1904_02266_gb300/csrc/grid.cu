@@ -20,7 +20,7 @@ namespace {
 
 inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 256;   // one thread per 8-bit digit in the histogram and scatter
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
@@ -67,19 +67,50 @@ __global__ void scan_single_block_kernel(uint32_t* __restrict__ data, int len) {
   }
 }
 
+static_assert(kSortThreads == 256, "the sort kernels give each digit one thread");
+
+// Sorts of at most this many tiles skip the scan launch: every scatter block
+// forms its own digit offsets from the raw histogram.
+constexpr int kFusedScanTiles = 64;
+
 // Stable scatter: within a block, elements are ranked in index order
 // (round-major, then thread), using match_any for ties inside a warp and
-// per-warp digit counts across warps.
+// per-warp digit counts across warps. With `scanned` the histogram holds the
+// exclusive scan of the digit-major counts; without, the raw counts (at most
+// kFusedScanTiles blocks), which the block scans itself: the offset of digit
+// d in block b is the count of smaller digits in all blocks plus the count of
+// digit d in the blocks before b.
 __global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys,
                                      const uint32_t* __restrict__ vals, int n, int shift,
-                                     const uint32_t* __restrict__ hist_scanned,
+                                     const uint32_t* __restrict__ hist, bool scanned,
                                      uint32_t* __restrict__ okeys, uint32_t* __restrict__ ovals) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t wc[kSortThreads / 32][256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   run[tid] = 0;
-  gbase[tid] = hist_scanned[tid * gridDim.x + blockIdx.x];
+  if (scanned) {
+    gbase[tid] = hist[tid * gridDim.x + blockIdx.x];
+  } else {
+    uint32_t tot = 0, before = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const uint32_t h = hist[tid * gridDim.x + b];
+      tot += h;
+      before += b < (int)blockIdx.x ? h : 0u;
+    }
+    // inclusive scan of the 256 digit totals (Hillis-Steele, in run[])
+    run[tid] = tot;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+      const uint32_t v = tid >= off ? run[tid - off] : 0u;
+      __syncthreads();
+      run[tid] += v;
+      __syncthreads();
+    }
+    gbase[tid] = run[tid] - tot + before;
+    __syncthreads();
+    run[tid] = 0;
+  }
 #pragma unroll
   for (int w = 0; w < kSortThreads / 32; ++w) wc[w][tid] = 0;
   __syncthreads();
@@ -392,9 +423,10 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int n, int bits, cu
   const int passes = (bits + 7) / 8;
   for (int p = 0; p < passes && e == cudaSuccess; ++p) {
     const int shift = 8 * p;
+    const bool fused = nb <= kFusedScanTiles;
     radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(ka, n, shift, hist);
-    scan_single_block_kernel<<<1, 1024, 0, s>>>(hist, 256 * nb);
-    radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(ka, va, n, shift, hist, kb, vb);
+    if (!fused) scan_single_block_kernel<<<1, 1024, 0, s>>>(hist, 256 * nb);
+    radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(ka, va, n, shift, hist, !fused, kb, vb);
     e = cudaGetLastError();
     uint32_t* t = ka; ka = kb; kb = t;
     t = va; va = vb; vb = t;

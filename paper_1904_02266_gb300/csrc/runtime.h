@@ -147,7 +147,8 @@ void release_bytes(cvo_ctx* ctx, size_t bytes);
 Cloud* get_cloud(cvo_ctx* ctx, int32_t h);
 int32_t add_cloud(cvo_ctx* ctx, Cloud* c);
 int create_cloud(cvo_ctx* ctx, const float* xyz, const float* feat, int64_t n, bool on_dev,
-                 cudaStream_t us, Cloud** out);
+                 cudaStream_t us, Cloud** out,
+                 bool wait = true);
 void free_cloud(cvo_ctx* ctx, Cloud* c);
 void free_plan(cvo_ctx* ctx, Plan* p);
 std::vector<double> ell_schedule(const cvo_params& p, int n);
